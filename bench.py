@@ -1,0 +1,489 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 GJP projector on the 512^3 cone-beam workload.
+
+Workload (default): 512^3 voxels (h = 1), circular cone beam at a 10 degree
+half-angle on the inscribed cylinder (D_so = 256/sin 10deg, D_sd = 2 D_so),
+512 x 512 detector, 360 views over 360 degrees; the volume is a seeded
+uniform [0, 1) random field (numpy default_rng(seed = rank)).
+
+One step is one pass of the whole hot path over that workload:
+  1. forward projection, float32 volume storage     (360 views)
+  2. forward projection, bfloat16 volume storage    (360 views)
+  3. adjoint (matched transpose) of the float32 projections into a float32 volume
+The metric is GJP samples per second (a sample is one (ray, plane) pair
+with at least one in-range tap, counted exactly on the host) over the
+whole step; per-kernel rates, bytes and roofline fractions are reported
+alongside.  All inputs (512 MiB volume, 377 MB projections) are larger
+than the 129 MB L2, so no L2 flush is inserted between iterations.
+
+    python bench.py [--steps K] [--warmup W] [--impl reference]
+    torchrun --nproc-per-node N bench.py --gpus N     (weak scaling: every
+        rank projects its own copy of the workload; no collective on the
+        data path)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "GJP Gsamples/s and achieved GB/s vs HBM peak, FP32 vs BF16 storage at stated error"
+UNIT = "Gsamples/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["gjp", "reference"], default="gjp")
+    p.add_argument("--n", type=int, default=512, help="volume edge (workload is defined at 512)")
+    p.add_argument("--views", type=int, default=360)
+    p.add_argument("--content", choices=["random", "phantom"], default="random")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU baseline sample")
+    return p.parse_args(argv)
+
+
+# --- workload ----------------------------------------------------------------
+
+def workload(args):
+    vg, cg = synth.scaled_c2_geometry(args.n, args.n, args.views, 10.0)
+    name = f"cone-beam GJP {args.n}^3 {args.content} volume, {args.n}^2 detector, {args.views} views, 10 deg half-angle"
+    return vg, cg, name
+
+
+def make_volume(args, vg, seed):
+    if args.content == "phantom":
+        return synth.voxelize(vg, supersample=2)
+    return synth.random_field(vg.n, seed=seed)
+
+
+def sample_counts(vg, cg) -> np.ndarray:
+    """Per view, the number of (ray, plane) pairs with at least one in-range
+    tap: planes i in [0, n_m - 1] with -1 < p_k(i) < n_k for both transverse
+    axes, evaluated in float64 from the geometry."""
+    n = np.array(vg.n, dtype=np.float64)
+    h = np.array(vg.h)
+    o = np.array(vg.origin)
+    iv, iu = np.meshgrid(np.arange(cg.nv, dtype=np.float64), np.arange(cg.nu, dtype=np.float64), indexing="ij")
+    out = np.zeros(cg.n_views, dtype=np.int64)
+    big = 1e18
+    for k in range(cg.n_views):
+        s = (cg.src[k] - o) / h
+        d = (cg.det_origin[k] + iu[..., None] * cg.det_u[k] + iv[..., None] * cg.det_v[k] - o) / h
+        r = d - s
+        m = np.argmax(np.abs(r), axis=-1)
+        rm = np.take_along_axis(r, m[..., None], -1)[..., 0]
+        sm = s[m]
+        lo = np.zeros(m.shape)
+        hi = n[m] - 1
+        for ax in range(3):
+            sel = m != ax
+            g = np.where(sel, r[..., ax] / rm, 0.0)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                a = sm + (-1.0 - s[ax]) / g
+                b = sm + (n[ax] - s[ax]) / g
+            low = np.where(g > 0, a, b)
+            upp = np.where(g > 0, b, a)
+            inside0 = (s[ax] > -1.0) & (s[ax] < n[ax])
+            low = np.where(g == 0, np.where(inside0, -big, big), low)
+            upp = np.where(g == 0, np.where(inside0, big, -big), upp)
+            low = np.where(sel, low, -big)
+            upp = np.where(sel, upp, big)
+            lo = np.maximum(lo, np.floor(low) + 1.0)
+            hi = np.minimum(hi, np.ceil(upp) - 1.0)
+        out[k] = int(np.maximum(hi - lo + 1.0, 0.0).sum())
+    return out
+
+
+# --- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def dram_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1609_00958_gb300", "csrc", "gjp.cu"), "rb").read()
+        if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        e = d["kernels"].get(kernel)
+        return None if e is None else float(e["bytes_per_launch"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
+
+
+# --- GPU arm -------------------------------------------------------------------
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def gpu_id_for_smi(local):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[local]
+        return str(local)
+
+
+def run_gjp(args):
+    import torch
+    from paper_1609_00958_gb300 import build as libbuild
+    libbuild.build()
+    import paper_1609_00958_gb300 as gjp
+
+    rank, world, local = dist_setup(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vg, cg, wname = workload(args)
+    geom = gjp.Geometry.from_cone(cg)
+    nvox = int(np.prod(vg.n))
+
+    vol_np = make_volume(args, vg, seed=rank)
+    vol32 = torch.from_numpy(vol_np).to(dev)
+    vol16 = vol32.to(torch.bfloat16)
+    proj32 = torch.empty(cg.n_views, cg.nv, cg.nu, device=dev)
+    proj16 = torch.empty_like(proj32)
+    back = torch.empty(vg.n, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    counts = sample_counts(vg, cg)
+    samples_per_kernel = int(counts.sum())
+    foot = np.array(gjp.footprint_voxels(geom, vg.n, vg.h, device=dev), dtype=np.float64)
+    proj_bytes = 4.0 * cg.n_views * cg.nu * cg.nv
+    alg_bytes = {
+        "forward_f32": 4.0 * foot.sum() + proj_bytes,
+        "forward_bf16": 2.0 * foot.sum() + proj_bytes,
+        "adjoint_f32": 8.0 * foot.sum() + proj_bytes,    # read-modify-write of each touched voxel per view
+    }
+
+    names = ["forward_f32", "forward_bf16", "adjoint_f32"]
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        gjp.forward(vol32, geom, vg.h, out=proj32)
+        if ev is not None:
+            ev[1].record(stream)
+        gjp.forward(vol16, geom, vg.h, out=proj16)
+        if ev is not None:
+            ev[2].record(stream)
+        gjp.adjoint(proj32, geom, vg.n, vg.h, out=back)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id_for_smi(local)) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.summary()
+    total_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(total_ms, world)
+    ms_per_step = total_ms / args.steps
+    per_kernel_ms = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
+                     for i, n in enumerate(names)}
+    samples_per_step = 3 * samples_per_kernel
+    value = samples_per_step * world / (ms_per_step * 1e-3) / 1e9
+
+    hbm, peak_kind = peaks()
+    kernels = {}
+    for n in names:
+        ms = per_kernel_ms[n]
+        gbs = alg_bytes[n] / (ms * 1e-3) / 1e9
+        kernels[n] = {"ms": round(ms, 4), "gsamples_s": round(samples_per_kernel / (ms * 1e-3) / 1e9, 2),
+                      "algorithmic_gb": round(alg_bytes[n] / 1e9, 4), "achieved_gbs": round(gbs, 1),
+                      "frac_of_" + peak_kind + "_hbm": round(gbs / hbm, 4),
+                      "paper_logical_gbs": round(samples_per_kernel * (8 if "bf16" in n else 16)
+                                                 / (ms * 1e-3) / 1e9, 1)}
+    dominant = max(names, key=lambda n: per_kernel_ms[n])
+    kmap = {"forward_f32": "gjp_forward_kernel<float", "forward_bf16": "gjp_forward_kernel<__nv_bfloat16",
+            "adjoint_f32": "gjp_adjoint_kernel"}
+    traffic = dram_traffic(kmap[dominant])
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": kernels[dominant]["achieved_gbs"],
+                "peak": hbm, "peak_kind": peak_kind + " (copy, MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
+                else "fallback", "unit": "GB/s",
+                "frac": round(kernels[dominant]["achieved_gbs"] / hbm, 4), "traffic": traffic}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, samples_per_step, world)
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (weights/accumulation); volume storage f32 and bf16",
+        "data": "synthetic (seeded uniform [0,1) random field)" if args.content == "random"
+        else "synthetic (Shepp-Logan-shaped phantom, project-owned ellipsoids)",
+        "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg.n_views,
+                   "step": "forward f32 + forward bf16 + adjoint f32", "samples_per_kernel": samples_per_kernel,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "kernels": kernels, "roofline": roofline, "clocks": clocks,
+        "gpu_launches": 3 * args.steps,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args, vg, cg, vol_np, counts, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, samples_per_step, world):
+    """Same step through the public API with host buffers: pinned host
+    volume in, projections and adjoint volume out, copies timed."""
+    import torch
+    h_vol32 = torch.from_numpy(vol_np).pin_memory()
+    h_vol16 = h_vol32.to(torch.bfloat16).pin_memory()
+    h_p32 = torch.empty(cg.n_views, cg.nv, cg.nu).pin_memory()
+    h_p16 = torch.empty_like(h_p32).pin_memory()
+    h_back = torch.empty(vg.n).pin_memory()
+    d_vol32 = torch.empty(vg.n, device=dev)
+    d_vol16 = torch.empty(vg.n, device=dev, dtype=torch.bfloat16)
+    d_p32 = torch.empty(cg.n_views, cg.nv, cg.nu, device=dev)
+    d_p16 = torch.empty_like(d_p32)
+    d_back = torch.empty(vg.n, device=dev)
+
+    def step():
+        d_vol32.copy_(h_vol32, non_blocking=True)
+        d_vol16.copy_(h_vol16, non_blocking=True)
+        gjp.forward(d_vol32, geom, vg.h, out=d_p32)
+        gjp.forward(d_vol16, geom, vg.h, out=d_p16)
+        gjp.adjoint(d_p32, geom, vg.n, vg.h, out=d_back)
+        h_p32.copy_(d_p32, non_blocking=True)
+        h_p16.copy_(d_p16, non_blocking=True)
+        h_back.copy_(d_back, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+        torch.cuda.synchronize()      # the host reads the step's results
+    wall = time.perf_counter() - t0
+    wall = max_over_ranks(wall, world)
+    bi = h_vol32.numel() * 4 + h_vol16.numel() * 2
+    bo = (h_p32.numel() + h_p16.numel() + h_back.numel()) * 4
+    return {"value": round(samples_per_step * world / (wall / args.steps) / 1e9, 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+            "ms_per_step": round(1e3 * wall / args.steps, 3)}
+
+
+# --- CPU oracle (baseline leg and reference arm) ----------------------------------
+
+def oracle_step(oracle, vg, cg, vol_np, vol_bf16w, view, threads, counts):
+    sub = cg.subset([view])
+    t0 = time.perf_counter()
+    p = oracle.forward(vol_np, vg, sub, threads=threads)
+    oracle.forward(vol_bf16w, vg, sub, threads=threads)
+    oracle.adjoint(p, vg, sub, threads=threads, max_bytes=16e9)
+    dt = time.perf_counter() - t0
+    return dt, 3 * int(counts[view])
+
+
+def bf16_widened(vol_np):
+    """Round-to-nearest-even float32 -> bfloat16, widened back to float32
+    (the values a bfloat16 volume stores)."""
+    import torch
+    return torch.from_numpy(vol_np).to(torch.bfloat16).float().numpy()
+
+
+def cpu_baseline(args, vg, cg, vol_np, counts, budget_s):
+    import oracle
+    threads = os.cpu_count() or 1
+    vol_w = bf16_widened(vol_np)
+    views = list(range(0, cg.n_views, max(1, cg.n_views // 36)))
+    t_tot, s_tot, used = 0.0, 0, []
+    for v in views:
+        dt, s = oracle_step(oracle, vg, cg, vol_np, vol_w, v, threads, counts)
+        t_tot += dt
+        s_tot += s
+        used.append(v)
+        if t_tot >= budget_s:
+            break
+    return {"value": round(s_tot / t_tot / 1e9, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle (OpenMP, {threads} threads) on {len(used)} of {cg.n_views} views "
+                      f"(views {used[0]}..{used[-1]} step {views[1] - views[0] if len(views) > 1 else 0}): "
+                      "forward f32 + forward bf16-stored + adjoint per view, same volume and geometry"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    vg, cg, wname = workload(args)
+    vol_np = make_volume(args, vg, seed=0)
+    vol_w = bf16_widened(vol_np)
+    counts = sample_counts(vg, cg)
+    threads = os.cpu_count() or 1
+    stride = max(1, cg.n_views // max(1, args.steps + args.warmup))
+    order = [(k * stride) % cg.n_views for k in range(args.steps + args.warmup)]
+    for v in order[:args.warmup]:
+        oracle_step(oracle, vg, cg, vol_np, vol_w, v, threads, counts)
+    times, samples = [], 0
+    for v in order[args.warmup:]:
+        dt, s = oracle_step(oracle, vg, cg, vol_np, vol_w, v, threads, counts)
+        times.append(dt)
+        samples += s
+    total = sum(times)
+    value = samples / total / 1e9
+    sample = (f"one view per step (forward f32 + forward bf16-stored + adjoint), views {order[args.warmup:]}, "
+              f"FP64 oracle with {threads} OpenMP threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / max(1, len(times)), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded uniform [0,1) random field)" if args.content == "random" else "synthetic phantom",
+        "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg.n_views,
+                   "step": "one view: forward f32 + forward bf16 + adjoint (oracle)"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gjp(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+/*
+ * gjp.h -- C ABI of the GB300 (sm_103a) branchless generalized Joseph
+ * projector (GJP): cone-beam forward projection of a voxel volume and its
+ * matched adjoint.
+ *
+ * Method: J. Graetz, "High performance volume ray casting: A branchless
+ * generalized Joseph projector" -- Algorithm 1 with Eq. 1-13.  For every
+ * detector pixel of every view the source-to-pixel ray is marched plane by
+ * plane along its dominant ("driving") axis m (Eq. 3), sampled at the
+ * integer planes p_m = 0 .. n_m - 1 (Eq. 5-6), the volume is interpolated
+ * bilinearly among the four neighbours in each plane (Eq. 7-12, w_lin of
+ * Eq. 13) and the samples are summed with the path-length weight |rt|
+ * (Algorithm 1) -- here |h (.) rt|, the world length of one plane step for
+ * voxel size h.  Taps outside the grid read zero.
+ *
+ * Conventions shared by every entry point
+ *  - Volume: C-contiguous [nx][ny][nz] (z fastest), voxel (i,j,k) centred at
+ *    world origin + (i*hx, j*hy, k*hz).  origin == NULL means the centred
+ *    grid, origin_k = -(n_k - 1)/2 * h_k.
+ *  - Projections: C-contiguous float32 [n_views][nv][nu] (iu fastest).
+ *    Pixel (iu, iv) of view k is centred at
+ *    det_origin[k] + iu*det_u[k] + iv*det_v[k]  (world units).
+ *  - Output unit: world length x volume value.
+ *  - Device pointers are caller-owned CUDA device memory on the current
+ *    device; the library never frees them.  `stream` is a cudaStream_t
+ *    (NULL = legacy default stream).  Calls are stream-ordered and
+ *    asynchronous; nothing synchronises the host.
+ *  - Errors are returned, never raised (no abort/exit/trap).  A kernel
+ *    failure that is only detected asynchronously surfaces from the CUDA
+ *    runtime on a later synchronisation, as for any CUDA library.
+ *  - The first call for a given (geometry, device, volume grid) builds and
+ *    uploads a per-view table (a few dozen bytes per view, allocated with
+ *    cudaMalloc and owned by the geometry).  Make that first call before
+ *    capturing a stream into a CUDA graph; later calls only launch kernels.
+ */
+#ifndef GJP_H
+#define GJP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GJP_OK = 0,
+    GJP_ERR_INVALID_ARG = 1, /* a pointer, size or geometry value is rejected */
+    GJP_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. dtype for adjoint) */
+    GJP_ERR_OOM = 3,         /* host or device allocation failed */
+    GJP_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    GJP_ERR_INTERNAL = 5,
+    GJP_ERR_TIMEOUT = 6
+} gjp_status;
+
+/* Storage type of the volume read by gjp_forward.  16-bit volumes are
+ * widened to float32 on load; interpolation weights and accumulation are
+ * float32 for every storage type. */
+typedef enum { GJP_F32 = 0, GJP_BF16 = 1, GJP_F16 = 2 } gjp_dtype;
+
+/* Opaque, library-owned projection geometry. */
+typedef struct gjp_geometry gjp_geometry;
+
+/*
+ * gjp_geometry_create -- describe n_views flat-panel cone-beam views (the
+ * source point s and pixel locations d that define the rays of Algorithm 1,
+ * Eq. 1-2).
+ *   src, det_origin, det_u, det_v : host arrays [n_views][3] of doubles in
+ *       world units (source position; centre of pixel (0,0); displacement
+ *       per +1 in iu; displacement per +1 in iv).  They are copied; the
+ *       caller keeps ownership.
+ *   nu, nv : detector columns (iu) and rows (iv), >= 1.
+ *   out    : receives the new geometry (set to NULL on error).
+ * Returns GJP_ERR_INVALID_ARG for n_views < 1, nu/nv < 1, NULL pointers,
+ * non-finite values, a zero or parallel det_u/det_v, or a source lying in
+ * its detector plane (which would allow a zero-length ray).  Host only: no
+ * CUDA call is made.
+ */
+gjp_status gjp_geometry_create(int n_views, int nu, int nv, const double *src,
+                               const double *det_origin, const double *det_u,
+                               const double *det_v, gjp_geometry **out);
+
+/* Frees the geometry and its device tables (NULL-safe).  Device tables are
+ * freed with cudaFree, which waits for work that may still use them. */
+void gjp_geometry_destroy(gjp_geometry *g);
+
+/* Reads back the detector shape of a geometry.  Any output pointer may be NULL. */
+gjp_status gjp_geometry_info(const gjp_geometry *g, int *n_views, int *nu, int *nv);
+
+/*
+ * gjp_forward -- GJP line integrals (Algorithm 1) of every pixel of every
+ * view of g through the volume.
+ *   d_volume : device, [nx][ny][nz] elements of `dtype` (2- or 4-byte
+ *              aligned as the type requires).
+ *   voxel_size : host double[3] (hx, hy, hz) > 0.
+ *   volume_origin : host double[3] world centre of voxel (0,0,0), or NULL.
+ *   d_proj   : device float32 [n_views][nv][nu]; fully overwritten.
+ * Returns GJP_ERR_INVALID_ARG for NULL pointers, sizes < 1, bad voxel size,
+ * an unknown dtype, or a source inside the volume's bounding box (the
+ * method integrates the whole line through the volume, which assumes
+ * source and detector outside it).
+ */
+gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
+                       const double voxel_size[3], const double volume_origin[3],
+                       const gjp_geometry *g, float *d_proj, void *stream);
+
+/*
+ * gjp_adjoint -- matched transpose of gjp_forward (float32 volume):
+ * d_volume (+)= A^T d_proj, where A is the system matrix of gjp_forward
+ * (the g = A f view of the reconstruction section).  Every (ray, plane,
+ * tap) triple of the forward pass scatters proj * |h (.) rt| * weight into
+ * its voxel, so <A x, y> = <x, A^T y> up to float32 rounding.
+ *   d_proj   : device float32 [n_views][nv][nu].
+ *   d_volume : device float32 [nx][ny][nz]; zeroed first unless
+ *              `accumulate` is non-zero.
+ * The scatter uses float32 atomic additions, so the summation order (and
+ * the last bits of the result) can differ between runs.
+ * Errors as for gjp_forward.
+ */
+gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, int64_t ny,
+                       int64_t nz, const double voxel_size[3], const double volume_origin[3],
+                       float *d_volume, int accumulate, void *stream);
+
+/*
+ * gjp_footprint -- measurement helper (not part of the method): sets
+ * d_marks[voxel] = 1 for every voxel that receives a non-zero
+ * interpolation weight from some ray of view `view` (the view's compulsory
+ * volume traffic, used for roofline accounting).  d_marks is device memory
+ * of nx*ny*nz bytes, zeroed by the caller; other bytes are left unchanged.
+ * Errors as for gjp_forward, plus GJP_ERR_INVALID_ARG for a view index
+ * outside [0, n_views).
+ */
+gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny, int64_t nz,
+                         const double voxel_size[3], const double volume_origin[3],
+                         unsigned char *d_marks, void *stream);
+
+/* Static, human-readable name of a status code. */
+const char *gjp_status_string(gjp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GJP_H */

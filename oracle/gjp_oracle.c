@@ -268,7 +268,7 @@ int gjp_oracle_ray_info(int64_t nx, int64_t ny, int64_t nz, const double h[3], c
  * Adjoint (transpose) of gjp_oracle_forward: vol_out += A^T proj.
  * vol_out: [nx][ny][nz] doubles; the caller zeroes it for a plain A^T y.
  * With nthreads > 1 each thread scatters into a private copy that is summed
- * afterwards (only when the copies fit in max_bytes; otherwise serial).
+ * afterwards; the thread count is reduced until the copies fit in max_bytes.
  */
 int gjp_oracle_adjoint(const double *proj, int64_t nx, int64_t ny, int64_t nz, const double h[3],
                        const double origin[3], int n_views, int nu, int nv, const double *src,
@@ -286,7 +286,10 @@ int gjp_oracle_adjoint(const double *proj, int64_t nx, int64_t ny, int64_t nz, c
 #ifdef _OPENMP
     T = nthreads > 0 ? nthreads : omp_get_max_threads();
 #endif
-    if (T > 1 && (double)T * (double)nvox * 8.0 > max_bytes) T = 1;
+    if (T > 1 && (double)T * (double)nvox * 8.0 > max_bytes) {
+        T = (int)(max_bytes / ((double)nvox * 8.0));
+        if (T < 1) T = 1;
+    }
     if (T <= 1) {
         for (int64_t ray = 0; ray < n_rays; ++ray) {
             const int view = (int)(ray / ((int64_t)nv * nu));

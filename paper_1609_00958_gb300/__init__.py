@@ -1,0 +1,149 @@
+"""GB300-native branchless generalized Joseph projector (GJP).
+
+Thin PyTorch-facing layer over the C ABI of ``libgjp.so`` (``include/gjp.h``):
+torch supplies device memory and the current CUDA stream; every step of the
+projection runs in the library's CUDA kernels.  There is no CPU fallback --
+calls raise if the library is missing or a tensor is not on a CUDA device.
+
+    geom = Geometry(src, det_origin, det_u, det_v, nu, nv)   # float64 (n_views, 3)
+    proj = forward(volume, geom, voxel_size=(1, 1, 1))         # (n_views, nv, nu) float32
+    back = adjoint(proj, geom, volume.shape, voxel_size=(1, 1, 1))
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _capi
+from ._capi import GjpError
+
+__all__ = ["Geometry", "forward", "adjoint", "footprint_voxels", "GjpError", "library_path"]
+
+
+def library_path() -> str:
+    return _capi.LIB_PATH
+
+
+class Geometry:
+    """Owns a ``gjp_geometry`` handle (host copy of the per-view source and
+    detector frames; device tables are built on first use per device)."""
+
+    def __init__(self, src, det_origin, det_u, det_v, nu: int, nv: int):
+        src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 3)
+        self.n_views = int(src.shape[0])
+        self.nu, self.nv = int(nu), int(nv)
+        st, h = _capi.gjp_geometry_create(self.n_views, self.nu, self.nv, src, det_origin, det_u, det_v)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_geometry_create")
+        self.handle = h
+
+    @classmethod
+    def from_cone(cls, cg) -> "Geometry":
+        """From any object with ``src, det_origin, det_u, det_v, nu, nv``."""
+        return cls(cg.src, cg.det_origin, cg.det_u, cg.det_v, cg.nu, cg.nv)
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            _capi.gjp_geometry_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def proj_shape(self):
+        return (self.n_views, self.nv, self.nu)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    m = {torch.float32: _capi.GJP_F32, torch.bfloat16: _capi.GJP_BF16, torch.float16: _capi.GJP_F16}
+    if t.dtype not in m:
+        raise TypeError(f"volume dtype {t.dtype} is not float32/bfloat16/float16")
+    return m[t.dtype]
+
+
+def _check_cuda(t, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the projector has no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be C-contiguous")
+
+
+def _stream(t, stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(t.device)
+    return int(stream.cuda_stream)
+
+
+def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None, out=None, stream=None):
+    """GJP forward projection (Algorithm 1) of a ``(nx, ny, nz)`` CUDA
+    volume (float32, bfloat16 or float16 storage) into ``(n_views, nv, nu)``
+    float32 projections."""
+    torch = _torch()
+    _check_cuda(volume, "volume")
+    if volume.dim() != 3:
+        raise ValueError("volume must be 3-D (nx, ny, nz)")
+    if out is None:
+        out = torch.empty(geometry.proj_shape, dtype=torch.float32, device=volume.device)
+    _check_cuda(out, "out")
+    if out.dtype != torch.float32 or tuple(out.shape) != geometry.proj_shape or out.device != volume.device:
+        raise ValueError("out must be float32 (n_views, nv, nu) on the volume's device")
+    with torch.cuda.device(volume.device):
+        st = _capi.gjp_forward(volume.data_ptr(), _dtype_code(volume), *volume.shape, voxel_size, origin,
+                               geometry.handle, out.data_ptr(), _stream(volume, stream))
+    if st != _capi.GJP_OK:
+        raise GjpError(st, "gjp_forward")
+    return out
+
+
+def adjoint(proj, geometry: Geometry, shape, voxel_size=(1.0, 1.0, 1.0), origin=None, out=None,
+            accumulate: bool = False, stream=None):
+    """Matched transpose of :func:`forward`: ``A^T proj`` as a float32
+    ``shape`` volume (added into ``out`` when ``accumulate``)."""
+    torch = _torch()
+    _check_cuda(proj, "proj")
+    if proj.dtype != torch.float32 or tuple(proj.shape) != geometry.proj_shape:
+        raise ValueError("proj must be float32 (n_views, nv, nu)")
+    shape = tuple(int(s) for s in shape)
+    if out is None:
+        out = (torch.zeros if accumulate else torch.empty)(shape, dtype=torch.float32, device=proj.device)
+    _check_cuda(out, "out")
+    if out.dtype != torch.float32 or tuple(out.shape) != shape or out.device != proj.device:
+        raise ValueError("out must be a float32 volume of the given shape on proj's device")
+    with torch.cuda.device(proj.device):
+        st = _capi.gjp_adjoint(proj.data_ptr(), geometry.handle, *shape, voxel_size, origin, out.data_ptr(),
+                               1 if accumulate else 0, _stream(proj, stream))
+    if st != _capi.GJP_OK:
+        raise GjpError(st, "gjp_adjoint")
+    return out
+
+
+def footprint_voxels(geometry: Geometry, shape, voxel_size=(1.0, 1.0, 1.0), origin=None, views=None,
+                     device=None):
+    """Per view, the number of distinct voxels that receive a non-zero
+    interpolation weight (the view's compulsory volume traffic in voxels).
+    Measurement helper for roofline accounting."""
+    torch = _torch()
+    device = torch.device("cuda") if device is None else torch.device(device)
+    shape = tuple(int(s) for s in shape)
+    marks = torch.empty(shape, dtype=torch.uint8, device=device)
+    views = range(geometry.n_views) if views is None else views
+    counts = []
+    with torch.cuda.device(device):
+        for v in views:
+            marks.zero_()
+            st = _capi.gjp_footprint(geometry.handle, int(v), *shape, voxel_size, origin, marks.data_ptr(),
+                                     _stream(marks, None))
+            if st != _capi.GJP_OK:
+                raise GjpError(st, "gjp_footprint")
+            counts.append(torch.count_nonzero(marks))
+    return [int(c.item()) for c in counts]

@@ -1,0 +1,309 @@
+"""Parity of the CUDA projector (through the C ABI) with the FP64 oracle.
+
+Bar: max |gpu - oracle| <= 1e-5 * max |oracle| for float32 storage; for
+16-bit storage <= 1e-5 against the oracle on the stored (quantised) values
+and <= 5e-3 against the unquantised float32 volume.  Driving-axis ties
+follow reading C2 (see tests/parity.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.geometry import ConeGeometry, VolumeGeometry
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL16 = 5e-3
+
+
+@pytest.fixture(scope="module")
+def gjp():
+    from paper_1609_00958_gb300 import build
+    build.build()
+    import paper_1609_00958_gb300 as m
+    return m
+
+
+def _project(gjp, vol_np, vg, cg, dtype=torch.float32):
+    vol = torch.from_numpy(np.ascontiguousarray(vol_np)).to("cuda").to(dtype)
+    g = gjp.Geometry.from_cone(cg)
+    out = gjp.forward(vol, g, voxel_size=vg.h, origin=vg.origin)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64), vol
+
+
+def _full_check(gjp, vol_np, vg, cg, tol=TOL32, dtype=torch.float32):
+    gpu, _ = _project(gjp, vol_np, vg, cg, dtype)
+    ref = oracle.forward(vol_np, vg, cg)
+    views, ius, ivs = parity.all_rays(cg)
+    return parity.check_rays(gpu[views, ivs, ius], vol_np, vg, cg, views, ius, ivs,
+                             np.abs(ref).max(), tol, ref=ref[views, ivs, ius])
+
+
+# --- c1: 64^3 Shepp-Logan-shaped phantom, 32 views, 64x64 -------------------
+
+def test_c1_phantom_fp32_all_rays(gjp):
+    vg, cg = synth.c1_geometry()
+    vol = synth.voxelize(vg, supersample=2)
+    r = _full_check(gjp, vol, vg, cg)
+    assert r["n"] == 32 * 64 * 64
+
+
+def test_c1_random_field_fp32_all_rays(gjp):
+    vg, cg = synth.c1_geometry()
+    _full_check(gjp, synth.random_field(vg.n, seed=0), vg, cg)
+
+
+def test_c1_matches_analytic_phantom(gjp):
+    """GJP of the rasterised phantom vs closed-form ellipsoid integrals
+    (projection-quality experiment): same bounded discretisation error as
+    the oracle's."""
+    vg, cg = synth.c1_geometry()
+    ell = synth.ellipsoids_world(vg)
+    gpu, _ = _project(gjp, synth.voxelize(vg, ell, supersample=2), vg, cg)
+    ana = oracle.ellipsoid_project(ell, cg, sub=8)
+    assert np.abs(gpu - ana).sum() / np.abs(ana).sum() < 0.02
+
+
+# --- arbitrary geometry: z-driven rays, anisotropic voxels, ragged tiles ----
+
+@pytest.mark.parametrize("steep", [False, True])
+def test_random_geometry_ragged_detector(gjp, steep):
+    rng = np.random.default_rng(100 + steep)
+    vg = VolumeGeometry.centred((37, 29, 23), h=(0.8, 1.1, 1.3))
+    cg = synth.random_geometry(rng, vg, 5, 45, 37, steep=steep)
+    vol = rng.random(vg.n, dtype=np.float32)
+    r = _full_check(gjp, vol, vg, cg)
+    if steep:
+        m, _, _ = oracle.ray_info(vg, cg, *parity.all_rays(cg))
+        assert (m == 2).sum() > 100
+
+
+def test_off_centre_volume_origin(gjp):
+    rng = np.random.default_rng(7)
+    vg = VolumeGeometry((30, 34, 26), (1.0, 0.9, 1.2), (-12.0, -20.0, -9.0))
+    cg = synth.random_geometry(rng, vg, 3, 33, 31)
+    _full_check(gjp, rng.random(vg.n, dtype=np.float32), vg, cg)
+
+
+# --- 16-bit storage: float32 weights and accumulation ------------------------
+
+@pytest.mark.parametrize("dt", ["bfloat16", "float16"])
+@pytest.mark.parametrize("content", ["phantom", "random"])
+def test_16bit_storage(gjp, dt, content):
+    vg, cg = synth.c1_geometry()
+    vol = synth.voxelize(vg, supersample=2) if content == "phantom" else synth.random_field(vg.n, seed=3)
+    tdt = getattr(torch, dt)
+    gpu, tvol = _project(gjp, vol, vg, cg, tdt)
+    stored = tvol.float().cpu().numpy()               # exact widening of the stored values
+    views, ius, ivs = parity.all_rays(cg)
+    ref_q = oracle.forward(stored, vg, cg)
+    kernel = parity.check_rays(gpu[views, ivs, ius], stored, vg, cg, views, ius, ivs,
+                               np.abs(ref_q).max(), TOL32, ref=ref_q[views, ivs, ius])
+    ref = oracle.forward(vol, vg, cg)
+    total = parity.check_rays(gpu[views, ivs, ius], vol, vg, cg, views, ius, ivs,
+                              np.abs(ref).max(), TOL16, ref=ref[views, ivs, ius])
+    assert kernel["max_rel"] < 1e-5 and total["max_rel"] < TOL16
+
+
+# --- adjoint -----------------------------------------------------------------
+
+def _adjoint_gpu(gjp, y_np, vg, cg, accumulate_into=None):
+    g = gjp.Geometry.from_cone(cg)
+    y = torch.from_numpy(np.ascontiguousarray(y_np, dtype=np.float32)).cuda()
+    out = None if accumulate_into is None else torch.from_numpy(accumulate_into.astype(np.float32)).cuda()
+    res = gjp.adjoint(y, g, vg.n, voxel_size=vg.h, origin=vg.origin, out=out,
+                      accumulate=accumulate_into is not None)
+    torch.cuda.synchronize()
+    return res.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("steep", [False, True])
+def test_adjoint_matches_oracle_transpose(gjp, steep):
+    rng = np.random.default_rng(200 + steep)
+    vg = VolumeGeometry.centred((40, 36, 33), h=(1.0, 0.9, 1.1))
+    cg = synth.random_geometry(rng, vg, 4, 41, 35, steep=steep)
+    y = rng.standard_normal((cg.n_views, cg.nv, cg.nu)).astype(np.float32)
+    gpu = _adjoint_gpu(gjp, y, vg, cg)
+    ref = oracle.adjoint(y.astype(np.float64), vg, cg)
+    err = np.abs(gpu - ref).max() / np.abs(ref).max()
+    assert err <= TOL32, err
+
+
+def test_adjoint_accumulate(gjp):
+    rng = np.random.default_rng(5)
+    vg = VolumeGeometry.centred((20, 18, 16))
+    cg = synth.random_geometry(rng, vg, 2, 19, 17)
+    y = rng.random((cg.n_views, cg.nv, cg.nu)).astype(np.float32)
+    base = rng.random(vg.n).astype(np.float32)
+    a = _adjoint_gpu(gjp, y, vg, cg)
+    b = _adjoint_gpu(gjp, y, vg, cg, accumulate_into=base)
+    np.testing.assert_allclose(b, a + base, rtol=1e-5, atol=1e-5 * np.abs(a).max())
+
+
+def test_dot_test_differentiation_workload(gjp):
+    """<A x, y> = <x, A^T y> on the 256^3 / 180-view / 256^2 workload with
+    seeded Gaussian x and y.  The dot product is a sum of random-sign terms,
+    so its float32 error is measured against S = sqrt(sum_r (Ax)_r^2 y_r^2),
+    the natural scale of that sum; with positive (uniform) x, y there is no
+    cancellation and the plain relative error is used."""
+    vg, cg = synth.c4_geometry()
+    g = gjp.Geometry.from_cone(cg)
+    gen = torch.Generator(device="cuda")
+    for kind in ("gauss", "uniform"):
+        gen.manual_seed(1)
+        if kind == "gauss":
+            x = torch.randn(vg.n, device="cuda", generator=gen)
+            y = torch.randn(cg.n_views, cg.nv, cg.nu, device="cuda", generator=gen)
+        else:
+            x = torch.rand(vg.n, device="cuda", generator=gen)
+            y = torch.rand(cg.n_views, cg.nv, cg.nu, device="cuda", generator=gen)
+        ax = gjp.forward(x, g, voxel_size=vg.h)
+        aty = gjp.adjoint(y, g, vg.n, voxel_size=vg.h)
+        lhs = torch.sum(ax.double() * y.double()).item()
+        rhs = torch.sum(x.double() * aty.double()).item()
+        if kind == "gauss":
+            scale = torch.sqrt(torch.sum((ax.double() * y.double()) ** 2)).item()
+        else:
+            scale = abs(lhs)
+        assert abs(lhs - rhs) <= 1e-5 * scale, (kind, lhs, rhs, scale)
+
+
+def test_gradient_finite_differences_differentiation_workload(gjp):
+    """L(x) = 1/2 |A x - b|^2 is quadratic, so central differences equal
+    (A e_j)^T (A x - b) exactly; compare with the adjoint's A^T (A x - b) on
+    64 seeded voxels of the 256^3 workload."""
+    vg, cg = synth.c4_geometry()
+    g = gjp.Geometry.from_cone(cg)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2)
+    x = torch.randn(vg.n, device="cuda", generator=gen)
+    b = torch.randn(cg.n_views, cg.nv, cg.nu, device="cuda", generator=gen)
+    res = gjp.forward(x, g, voxel_size=vg.h) - b
+    grad = gjp.adjoint(res, g, vg.n, voxel_size=vg.h)
+    rng = np.random.default_rng(2)
+    # voxels inside the inscribed cylinder (seen by every view)
+    picks = []
+    while len(picks) < 64:
+        i, j, k = rng.integers(32, 224, size=3)
+        if (i - 127.5) ** 2 + (j - 127.5) ** 2 < 90 ** 2:
+            picks.append((int(i), int(j), int(k)))
+    eps = 1.0
+    for (i, j, k) in picks:
+        xp = x.clone(); xp[i, j, k] += eps
+        xm = x.clone(); xm[i, j, k] -= eps
+        rp = gjp.forward(xp, g, voxel_size=vg.h).double() - b.double()
+        rm = gjp.forward(xm, g, voxel_size=vg.h).double() - b.double()
+        fd = (0.5 * (rp ** 2).sum() - 0.5 * (rm ** 2).sum()).item() / (2 * eps)
+        gv = grad[i, j, k].item()
+        assert abs(fd - gv) <= 1e-4 * max(abs(gv), 1.0), (i, j, k, fd, gv)
+
+
+# --- full-size workload (512^3, 360 views, 512^2), sampled outputs -----------
+
+@pytest.mark.parametrize("content", ["phantom", "random"])
+def test_c2_full_size_sampled(gjp, content):
+    vg, cg = synth.c2_geometry()
+    vol = synth.voxelize(vg, supersample=2) if content == "phantom" else synth.random_field(vg.n, seed=0)
+    gpu, _ = _project(gjp, vol, vg, cg)
+    # one whole view (45 degrees: contains driving-axis ties) plus 4000 random rays
+    v45 = 45
+    views = np.full(cg.nu * cg.nv, v45)
+    iv, iu = np.meshgrid(np.arange(cg.nv), np.arange(cg.nu), indexing="ij")
+    sv, su, sw = parity.sampled_rays(cg, 4000, seed=9)
+    views = np.concatenate([views, sv]); ius = np.concatenate([iu.ravel(), su])
+    ivs = np.concatenate([iv.ravel(), sw])
+    ref = oracle.rays(vol, vg, cg, views, ius, ivs)
+    r = parity.check_rays(gpu[views, ivs, ius], vol, vg, cg, views, ius, ivs, np.abs(ref).max(),
+                          TOL32, ref=ref)
+    assert r["ties"] > 0   # the 45-degree view exercises reading C2
+
+
+# --- edge cases ----------------------------------------------------------------
+
+def test_tiny_and_degenerate_grids(gjp):
+    rng = np.random.default_rng(8)
+    for shape in [(1, 1, 1), (2, 1, 3), (1, 5, 1), (3, 3, 1)]:
+        vg = VolumeGeometry.centred(shape, h=(1.0, 1.5, 0.7))
+        cg = synth.random_geometry(rng, VolumeGeometry.centred((8, 8, 8)), 3, 3, 2)
+        vol = rng.random(shape, dtype=np.float32) + 0.5
+        _full_check(gjp, vol, vg, cg)
+
+
+def test_rays_missing_the_volume_are_exactly_zero(gjp):
+    vg = VolumeGeometry.centred((16, 16, 16))
+    cg = synth.circular(2, 64, 48, 60.0, 120.0, 3.0)     # panel much larger than the shadow
+    vol = np.ones(vg.n, dtype=np.float32)
+    gpu, _ = _project(gjp, vol, vg, cg)
+    ref = oracle.forward(vol, vg, cg)
+    assert (gpu[ref == 0.0] == 0.0).all() and (ref == 0.0).sum() > 1000
+    _full_check(gjp, vol, vg, cg)
+
+
+def test_axis_aligned_ray_column_sum(gjp):
+    vg = VolumeGeometry.centred((12, 10, 8), h=(0.5, 1.0, 2.0))
+    vol = np.random.default_rng(1).random(vg.n, dtype=np.float32)
+    idx = np.array([0, 4, 5])
+    centre = np.array(vg.origin) + idx * np.array(vg.h)
+    src = (centre - [100.0, 0, 0])[None]
+    cg = ConeGeometry(src, (centre + [100.0, 0, 0])[None], np.array([[0, 0, 1e-2]]),
+                      np.array([[0, 1e-2, 0]]), 1, 1)
+    gpu, _ = _project(gjp, vol, vg, cg)
+    want = vg.h[0] * vol[:, 4, 5].astype(np.float64).sum()
+    assert gpu[0, 0, 0] == pytest.approx(want, rel=2e-6)
+
+
+def test_source_inside_volume_is_rejected(gjp):
+    vg = VolumeGeometry.centred((300, 300, 300))
+    cg = synth.circular(2, 8, 8, 100.0, 200.0, 1.0)
+    vol = torch.zeros(vg.n, device="cuda")
+    g = gjp.Geometry.from_cone(cg)
+    with pytest.raises(gjp.GjpError) as e:
+        gjp.forward(vol, g)
+    assert e.value.status == 1
+
+
+def test_repeated_calls_reuse_table_and_are_deterministic(gjp):
+    vg, cg = synth.c1_geometry()
+    vol = torch.from_numpy(synth.random_field(vg.n, seed=4)).cuda()
+    g = gjp.Geometry.from_cone(cg)
+    a = gjp.forward(vol, g).clone()
+    b = gjp.forward(vol, g)
+    assert torch.equal(a, b)
+    # a different grid on the same geometry builds a second table
+    c = gjp.forward(vol, g, voxel_size=(0.5, 0.5, 0.5))
+    assert not torch.equal(a, c)
+
+
+def test_int64_indexing_beyond_2_pow_31_elements(gjp):
+    """Maximum-size path: a bfloat16 volume with more than 2^31 voxels uses
+    64-bit offsets; sampled rays against the oracle."""
+    free, _ = torch.cuda.mem_get_info()
+    try:
+        import os
+        host_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2 ** 30
+    except (ValueError, OSError):
+        host_gb = 0
+    if free < 12 * 2 ** 30 or host_gb < 48:
+        pytest.skip("needs ~12 GB device and ~48 GB host memory")
+    n = (1300, 1300, 1300)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    vol = torch.rand(n, device="cuda", generator=gen).to(torch.bfloat16)
+    assert vol.numel() > 2 ** 31
+    vg = VolumeGeometry.centred(n)
+    cg = synth.cone_angle_geometry(1300, 96, 3, 10.0)
+    g = gjp.Geometry.from_cone(cg)
+    out = gjp.forward(vol, g).cpu().numpy().astype(np.float64)
+    stored = vol.float().cpu().numpy()
+    del vol
+    views, ius, ivs = parity.sampled_rays(cg, 300, seed=12)
+    ref = oracle.rays(stored, vg, cg, views, ius, ivs)
+    parity.check_rays(out[views, ivs, ius], stored, vg, cg, views, ius, ivs, np.abs(ref).max(), TOL32,
+                      ref=ref)
