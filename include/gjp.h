@@ -103,6 +103,35 @@ gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_
                        const double voxel_size[3], const double volume_origin[3],
                        const gjp_geometry *g, float *d_proj, void *stream);
 
+/* Kernel family used by gjp_forward_ex. */
+typedef enum {
+    GJP_PATH_AUTO = 0,   /* the library's fastest family for the call (currently GATHER) */
+    GJP_PATH_GATHER = 1, /* one thread per ray, taps gathered from global memory */
+    GJP_PATH_SLAB = 2,   /* detector tiles stream per-plane voxel boxes into shared memory
+                            with TMA; needs a 16-byte aligned volume whose z row is a
+                            multiple of 16 bytes and a magnification the box sizes cover */
+    GJP_PATH_PREFETCH = 3 /* gather, with each warp's footprint a few planes ahead
+                            prefetched into L2 by TMA; same volume alignment as SLAB */
+} gjp_path;
+
+/*
+ * gjp_forward_ex -- gjp_forward with an explicit kernel family.  Both
+ * families compute the same samples with the same arithmetic (results agree
+ * to float32 rounding).  GJP_PATH_SLAB returns GJP_ERR_UNSUPPORTED when its
+ * conditions are not met; GJP_PATH_AUTO never does.
+ */
+gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
+                          const double voxel_size[3], const double volume_origin[3],
+                          const gjp_geometry *g, float *d_proj, gjp_path path, void *stream);
+
+/*
+ * gjp_stream_status -- synchronises `stream` and reports whether any kernel
+ * of this library gave up a bounded wait since the last call
+ * (GJP_ERR_TIMEOUT; the flag is then cleared).  Such a kernel returns
+ * without hanging the device but its output is not valid.
+ */
+gjp_status gjp_stream_status(void *stream);
+
 /*
  * gjp_adjoint -- matched transpose of gjp_forward (float32 volume):
  * d_volume (+)= A^T d_proj, where A is the system matrix of gjp_forward

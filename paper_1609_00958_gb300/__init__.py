@@ -16,7 +16,7 @@ import numpy as np
 from . import _capi
 from ._capi import GjpError
 
-__all__ = ["Geometry", "forward", "adjoint", "footprint_voxels", "GjpError", "library_path"]
+__all__ = ["Geometry", "forward", "adjoint", "footprint_voxels", "stream_status", "GjpError", "library_path"]
 
 
 def library_path() -> str:
@@ -84,10 +84,15 @@ def _stream(t, stream):
     return int(stream.cuda_stream)
 
 
-def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None, out=None, stream=None):
+_PATHS = {"auto": 0, "gather": 1, "slab": 2, "prefetch": 3}
+
+
+def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None, out=None, stream=None,
+            path: str = "auto"):
     """GJP forward projection (Algorithm 1) of a ``(nx, ny, nz)`` CUDA
     volume (float32, bfloat16 or float16 storage) into ``(n_views, nv, nu)``
-    float32 projections."""
+    float32 projections.  ``path`` selects the kernel family ("auto",
+    "gather" or "slab"; see ``gjp_forward_ex``)."""
     torch = _torch()
     _check_cuda(volume, "volume")
     if volume.dim() != 3:
@@ -98,8 +103,8 @@ def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None,
     if out.dtype != torch.float32 or tuple(out.shape) != geometry.proj_shape or out.device != volume.device:
         raise ValueError("out must be float32 (n_views, nv, nu) on the volume's device")
     with torch.cuda.device(volume.device):
-        st = _capi.gjp_forward(volume.data_ptr(), _dtype_code(volume), *volume.shape, voxel_size, origin,
-                               geometry.handle, out.data_ptr(), _stream(volume, stream))
+        st = _capi.gjp_forward_ex(volume.data_ptr(), _dtype_code(volume), *volume.shape, voxel_size, origin,
+                                  geometry.handle, out.data_ptr(), _PATHS[path], _stream(volume, stream))
     if st != _capi.GJP_OK:
         raise GjpError(st, "gjp_forward")
     return out
@@ -147,3 +152,14 @@ def footprint_voxels(geometry: Geometry, shape, voxel_size=(1.0, 1.0, 1.0), orig
                 raise GjpError(st, "gjp_footprint")
             counts.append(torch.count_nonzero(marks))
     return [int(c.item()) for c in counts]
+
+
+def stream_status(stream=None):
+    """Synchronise the stream and raise if a kernel of the library gave up a
+    bounded wait since the last check (its output is then invalid)."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = _capi.gjp_stream_status(int(stream.cuda_stream))
+    if st != _capi.GJP_OK:
+        raise GjpError(st, "gjp_stream_status")

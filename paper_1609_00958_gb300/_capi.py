@@ -26,9 +26,14 @@ GJP_F32 = 0
 GJP_BF16 = 1
 GJP_F16 = 2
 
+GJP_PATH_AUTO = 0
+GJP_PATH_GATHER = 1
+GJP_PATH_SLAB = 2
+GJP_PATH_PREFETCH = 3
+
 #: every symbol include/gjp.h declares
 EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_forward",
-           "gjp_adjoint", "gjp_footprint", "gjp_status_string")
+           "gjp_forward_ex", "gjp_stream_status", "gjp_adjoint", "gjp_footprint", "gjp_status_string")
 
 _lib = None
 _P = ctypes.c_void_p
@@ -60,6 +65,10 @@ def load(path: str | None = None):
     lib.gjp_geometry_info.restype = _I
     lib.gjp_forward.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _P]
     lib.gjp_forward.restype = _I
+    lib.gjp_forward_ex.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _I, _P]
+    lib.gjp_forward_ex.restype = _I
+    lib.gjp_stream_status.argtypes = [_P]
+    lib.gjp_stream_status.restype = _I
     lib.gjp_adjoint.argtypes = [_P, _P, _I64, _I64, _I64, _D3, _D3, _P, _I, _P]
     lib.gjp_adjoint.restype = _I
     lib.gjp_footprint.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P]
@@ -117,6 +126,17 @@ def gjp_forward(d_volume: int, dtype: int, nx: int, ny: int, nz: int, voxel_size
     return load().gjp_forward(_P(d_volume), int(dtype), int(nx), int(ny), int(nz), _d3(voxel_size),
                               _d3(volume_origin), _P(geometry) if geometry else None, _P(d_proj),
                               _P(stream))
+
+
+def gjp_forward_ex(d_volume: int, dtype: int, nx: int, ny: int, nz: int, voxel_size, volume_origin,
+                   geometry, d_proj: int, path: int, stream: int) -> int:
+    return load().gjp_forward_ex(_P(d_volume), int(dtype), int(nx), int(ny), int(nz), _d3(voxel_size),
+                                 _d3(volume_origin), _P(geometry) if geometry else None, _P(d_proj), int(path),
+                                 _P(stream))
+
+
+def gjp_stream_status(stream: int) -> int:
+    return load().gjp_stream_status(_P(stream))
 
 
 def gjp_adjoint(d_proj: int, geometry, nx: int, ny: int, nz: int, voxel_size, volume_origin,

@@ -33,6 +33,8 @@
 //    that accompanies Algorithm 1).
 #include "gjp.h"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -41,6 +43,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -63,10 +66,16 @@ struct VolParams {
 };
 
 #ifndef GJP_TILE_U
-#define GJP_TILE_U 8
+#define GJP_TILE_U 4
 #endif
 #ifndef GJP_BATCH
 #define GJP_BATCH 4
+#endif
+#ifndef GJP_MIN_BLOCKS
+#define GJP_MIN_BLOCKS 8      // 8 blocks of 128 threads: 64 registers per thread
+#endif
+#ifndef GJP_SLAB_MIN_BLOCKS
+#define GJP_SLAB_MIN_BLOCKS 3
 #endif
 constexpr int kTileV = 32;          // lanes of a warp along v (contiguous z)
 constexpr int kTileU = GJP_TILE_U;  // warps of a block along u
@@ -77,6 +86,7 @@ struct gjp_cache_entry {
     int device;
     double key[9];
     ViewParams *d_table;
+    int box_rows, box_cols4, box_cols8;   // slab box sizes for this grid (0 = not computed)
 };
 
 }  // namespace
@@ -85,7 +95,7 @@ struct gjp_geometry {
     int n_views, nu, nv;
     std::vector<double> src, org, du, dv;
     std::mutex mu;
-    std::vector<gjp_cache_entry> cache;
+    std::deque<gjp_cache_entry> cache;   // deque: entries keep their address
 };
 
 namespace {
@@ -127,18 +137,19 @@ void build_table(const gjp_geometry &g, const int64_t n[3], const double h[3], c
     }
 }
 
-// Returns the device table for (g, current device, grid); builds it on first use.
+// Returns the cache entry (device table) for (g, current device, grid);
+// builds it on first use.
 gjp_status get_table(const gjp_geometry *gc, const int64_t n[3], const double h[3], const double o[3],
-                     const ViewParams **out)
+                     gjp_cache_entry **out)
 {
     gjp_geometry *g = const_cast<gjp_geometry *>(gc);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GJP_ERR_CUDA;
     double key[9] = {(double)n[0], (double)n[1], (double)n[2], h[0], h[1], h[2], o[0], o[1], o[2]};
     std::lock_guard<std::mutex> lock(g->mu);
-    for (const auto &e : g->cache) {
+    for (auto &e : g->cache) {
         if (e.device == dev && std::memcmp(e.key, key, sizeof key) == 0) {
-            *out = e.d_table;
+            *out = &e;
             return GJP_OK;
         }
     }
@@ -162,8 +173,14 @@ gjp_status get_table(const gjp_geometry *gc, const int64_t n[3], const double h[
     e.device = dev;
     std::memcpy(e.key, key, sizeof key);
     e.d_table = d;
-    g->cache.push_back(e);
-    *out = d;
+    e.box_rows = e.box_cols4 = e.box_cols8 = 0;
+    try {
+        g->cache.push_back(e);
+    } catch (const std::bad_alloc &) {
+        cudaFree(d);
+        return GJP_ERR_OOM;
+    }
+    *out = &g->cache.back();
     return GJP_OK;
 }
 
@@ -250,6 +267,10 @@ template <> __device__ __forceinline__ float load_voxel<__nv_bfloat16>(const __n
     return __bfloat162float(__ldg(p));
 }
 template <> __device__ __forceinline__ float load_voxel<__half>(const __half *p) { return __half2float(__ldg(p)); }
+
+__device__ __forceinline__ float to_float(float x) { return x; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
 
 // ---------------------------------------------------------------------------
 // Per-ray setup.
@@ -467,7 +488,7 @@ __device__ __forceinline__ float march_boundary(const T *__restrict__ vol, const
 }
 
 template <typename T, typename Index>
-__global__ void __launch_bounds__(kThreads) gjp_forward_kernel(
+__global__ void __launch_bounds__(kThreads, GJP_MIN_BLOCKS) gjp_forward_kernel(
     const T *__restrict__ vol, VolParams V, const ViewParams *__restrict__ views,
     int nu, int nv, int n_tv, float *__restrict__ proj)
 {
@@ -483,6 +504,390 @@ __global__ void __launch_bounds__(kThreads) gjp_forward_kernel(
     setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
 
     float acc = (R.m != 2) ? march_interior<T, Index, true>(vol, R) : march_interior<T, Index, false>(vol, R);
+    acc += march_boundary<T, Index>(vol, R);
+    proj[((size_t)view * nv + iv) * nu + iu] = acc * R.step;
+}
+
+// ---------------------------------------------------------------------------
+// Forward projection, shared-memory slab pipeline.
+//
+// A block owns a tile of kSlabWarps detector columns x 32 detector rows.
+// When every ray of the tile shares its driving axis (x or y), the rays
+// advance through the same sequence of planes.  The planes are taken
+// kPlanes at a time (a "stage"): the producer warp computes, from the
+// tile's four corner rays at the stage's first and last plane (a plane's
+// crossings are a projective image of the tile, so their extremes sit at the
+// corners, and each ray moves linearly from plane to plane), the box of
+// voxels the stage's taps can touch, and one TMA tensor load brings that
+// kPlanes x rows x cols box into a ring of shared-memory stages.  The
+// consumer warps read their taps from shared memory.  Out-of-range parts of
+// a box are zero-filled by the TMA unit, which is exactly the zero-border
+// reading of "p is in volume".  Stages whose box would not fit, and tiles
+// with mixed driving axes, use the global-memory gather above.
+
+constexpr int kSlabWarps = 8;
+constexpr int kSlabThreads = (kSlabWarps + 1) * 32;
+constexpr int kStages = 4;       // ring depth
+constexpr int kPlanes = 4;       // planes per stage
+constexpr int kBoxRMax = 24;     // largest box extent along the non-contiguous transverse axis
+constexpr unsigned kSpinLimit = 1u << 22;
+
+// Set by a kernel whose bounded wait gave up; read and cleared by
+// gjp_stream_status().
+__device__ unsigned g_gjp_status;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and the status word set) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (unsigned spin = 0; spin < kSpinLimit; ++spin)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(&g_gjp_status, 1u);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, unsigned long long *bar, int c0,
+                                            int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_addr(bar)), "r"(c0),
+        "r"(c1), "r"(c2)
+        : "memory");
+}
+
+struct SlabShared {
+    unsigned long long full[kStages], empty[kStages];
+    int4 hdr[kStages];              // a0, b0, box fits, unused
+    long long corner[4][4];         // Pa, Ga, Pb, Gb of the tile's corner rays
+    int sweep_lo, sweep_hi, m_first, mixed;
+};
+
+template <typename T, typename Index, int kBoxC>
+__global__ void __launch_bounds__(kSlabThreads, GJP_SLAB_MIN_BLOCKS) gjp_forward_slab_kernel(
+    const T *__restrict__ vol, VolParams V, const ViewParams *__restrict__ views, int nu, int nv, int n_tv,
+    const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y, int box_r,
+    float *__restrict__ proj)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int kAlign = 16 / (int)sizeof(T);               // TMA x coordinate granularity
+    const int stage_elems = kPlanes * box_r * kBoxC;
+    const int stage_bytes = (stage_elems * (int)sizeof(T) + 127) & ~127;
+    SlabShared &S = *reinterpret_cast<SlabShared *>(smem_raw + kStages * stage_bytes);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp == kSlabWarps;
+    const int tile = blockIdx.x, view = blockIdx.y;
+    const int v_base = (tile % n_tv) * 32, u_base = (tile / n_tv) * kSlabWarps;
+    const int iv = v_base + lane, iu = u_base + warp;
+    const bool have_ray = !producer && iv < nv && iu < nu;
+
+    if (threadIdx.x == 0) {
+        S.sweep_lo = 0x7fffffff;
+        S.sweep_hi = -1;
+        S.m_first = -1;
+        S.mixed = 0;
+        for (int k = 0; k < kStages; ++k) {
+            mbar_init(&S.full[k], 1);
+            mbar_init(&S.empty[k], kSlabWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    Ray R;
+    if (have_ray) {
+        ViewParams vp;
+        load_view(views, view, vp);
+        setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
+        if (R.s_lo <= R.s_hi) {
+            atomicMin(&S.sweep_lo, R.s_lo);
+            atomicMax(&S.sweep_hi, R.s_hi);
+        }
+        atomicCAS(&S.m_first, -1, R.m);
+    }
+    __syncthreads();
+    if (have_ray) {
+        if (R.m != S.m_first) S.mixed = 1;
+        const int u_last = min(kSlabWarps, nu - u_base) - 1, v_last = min(32, nv - v_base) - 1;
+        // a thread may be several corners when the tile is one ray wide
+        for (int cu = 0; cu < 2; ++cu)
+            for (int cv = 0; cv < 2; ++cv)
+                if ((cu == 0 ? warp == 0 : warp == u_last) && (cv == 0 ? lane == 0 : lane == v_last)) {
+                    long long *c = S.corner[2 * cu + cv];
+                    c[0] = R.Pa;
+                    c[1] = R.Ga;
+                    c[2] = R.Pb;
+                    c[3] = R.Gb;
+                }
+    }
+    __syncthreads();
+
+    const int m = S.m_first;
+    if (S.mixed || m < 0 || m == 2) {       // gather path for the whole tile
+        if (have_ray) {
+            float acc = (R.m != 2) ? march_interior<T, Index, true>(vol, R) : march_interior<T, Index, false>(vol, R);
+            acc += march_boundary<T, Index>(vol, R);
+            proj[((size_t)view * nv + iv) * nu + iu] = acc * R.step;
+        }
+        return;
+    }
+    const int I0 = S.sweep_lo, I1 = S.sweep_hi;
+    const int n_stages = I1 >= I0 ? (I1 - I0) / kPlanes + 1 : 0;
+    T *stages = reinterpret_cast<T *>(smem_raw);
+    const int stage_stride = stage_bytes / (int)sizeof(T);
+    // shared-memory layout of a box: plane x = i boxes are [plane][row][col],
+    // plane y = i boxes are [row][plane][col] (TMA writes dimension 0 fastest)
+    const int row_stride = m == 0 ? kBoxC : kPlanes * kBoxC;
+    const int plane_stride = m == 0 ? box_r * kBoxC : kBoxC;
+
+    if (producer) {
+        const int nm = V.n[m];
+        const int ic = (nm - 1) >> 1;
+        const unsigned tx = (unsigned)(stage_elems * (int)sizeof(T));
+        // lane l tracks corner l & 3 at the stage's first (l < 4) or last plane
+        const long long *cr = S.corner[lane & 3];
+        const long long Pa = cr[0], Ga = cr[1], Pb = cr[2], Gb = cr[3];
+        const int end = (lane >> 2) & 1;
+        int slot = 0;
+        unsigned phase = 0;
+        bool ok = true;
+        int st = 0;
+        for (; st < n_stages; ++st) {
+            if (st >= kStages) ok = mbar_wait(&S.empty[slot], phase ^ 1u);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            const int i0 = I0 + st * kPlanes;
+            const int i = end ? min(i0 + kPlanes - 1, I1) : i0;
+            const int fa = floor_of((unsigned long long)pos_at(Pa, Ga, i, ic));
+            const int fb = floor_of((unsigned long long)pos_at(Pb, Gb, i, ic));
+            const int amin = __reduce_min_sync(0xffffffffu, fa), amax = __reduce_max_sync(0xffffffffu, fa);
+            const int bmin = __reduce_min_sync(0xffffffffu, fb), bmax = __reduce_max_sync(0xffffffffu, fb);
+            if (lane == 0) {
+                // one voxel of margin below, taps reach floor + 1, one voxel of margin above
+                const int a0 = amin - 1;
+                const int b0 = (bmin - 1) & ~(kAlign - 1);
+                const bool fits = (amax + 3 - a0 <= box_r) && (bmax + 3 - b0 <= kBoxC);
+                S.hdr[slot] = make_int4(a0, b0, fits ? 1 : 0, 0);
+                if (fits) {
+                    mbar_arrive_expect_tx(&S.full[slot], tx);
+                    T *dst = stages + slot * stage_stride;
+                    if (m == 0) tma_load_3d(dst, &map_x, &S.full[slot], b0, a0, i0);   // planes x = i0 ..
+                    else tma_load_3d(dst, &map_y, &S.full[slot], b0, i0, a0);          // planes y = i0 ..
+                } else {
+                    mbar_arrive(&S.full[slot]);
+                }
+            }
+            if (++slot == kStages) {
+                slot = 0;
+                phase ^= 1u;
+            }
+        }
+        if (!ok && lane == 0) {
+            // a consumer stopped; wait (bounded) for the copies still in flight
+            for (int k = 0; k < kStages && k < st; ++k) {
+                if (--slot < 0) {
+                    slot = kStages - 1;
+                    phase ^= 1u;
+                }
+                mbar_wait(&S.full[slot], phase);
+            }
+        }
+        return;
+    }
+
+    // consumers
+    const unsigned na = have_ray ? (unsigned)R.na : 0u, nb = have_ray ? (unsigned)R.nb : 0u;
+    const Index sa = have_ray ? (Index)R.sa : 0, sb = have_ray ? (Index)R.sb : 0, sm = have_ray ? (Index)R.sm : 0;
+    unsigned long long pa = 0, pb = 0, ga = 0, gb = 0;
+    int s_lo = 1, s_hi = 0;
+    if (have_ray) {
+        pa = (unsigned long long)pos_at(R.Pa, R.Ga, I0, R.ic);
+        pb = (unsigned long long)pos_at(R.Pb, R.Gb, I0, R.ic);
+        ga = (unsigned long long)R.Ga;
+        gb = (unsigned long long)R.Gb;
+        s_lo = R.s_lo;
+        s_hi = R.s_hi;
+    }
+    const unsigned max_idx = (unsigned)(stage_elems - row_stride - 2);
+    float acc = 0.0f;
+    int slot = 0;
+    unsigned phase = 0;
+    bool ok = true;
+    for (int st = 0; st < n_stages; ++st) {
+        if (ok) ok = mbar_wait(&S.full[slot], phase);
+        const int4 h = S.hdr[slot];
+        const T *box = stages + slot * stage_stride;
+        const int i0 = I0 + st * kPlanes;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const int i = i0 + p;
+            if (ok && i >= s_lo && i <= s_hi) {
+                const float da = frac_of(pa), db = frac_of(pb);
+                const int ia = floor_of(pa), ib = floor_of(pb);
+                float v00, v01, v10, v11;
+                if (h.z) {
+                    // taps lie in the box by construction; the unsigned min only
+                    // guards the shared-memory bounds
+                    const unsigned idx = min((unsigned)((ia - h.x) * row_stride + (ib - h.y) + p * plane_stride),
+                                             max_idx);
+                    const T *s = box + idx;
+                    v00 = to_float(s[0]);
+                    v01 = to_float(s[1]);
+                    v10 = to_float(s[row_stride]);
+                    v11 = to_float(s[row_stride + 1]);
+                } else {
+                    const bool a0 = (unsigned)ia < na, a1 = (unsigned)(ia + 1) < na;
+                    const bool b0 = (unsigned)ib < nb, b1 = (unsigned)(ib + 1) < nb;
+                    const T *q = vol + ((Index)i * sm + (Index)ia * sa + (Index)ib * sb);
+                    v00 = (a0 && b0) ? load_voxel(q) : 0.0f;
+                    v01 = (a0 && b1) ? load_voxel(q + sb) : 0.0f;
+                    v10 = (a1 && b0) ? load_voxel(q + sa) : 0.0f;
+                    v11 = (a1 && b1) ? load_voxel(q + sa + sb) : 0.0f;
+                }
+                const float e0 = __fmaf_rn(db, v01 - v00, v00);
+                const float e1 = __fmaf_rn(db, v11 - v10, v10);
+                acc += __fmaf_rn(da, e1 - e0, e0);
+            }
+            pa += ga;
+            pb += gb;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[slot]);
+        if (++slot == kStages) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+    if (have_ray) proj[((size_t)view * nv + iv) * nu + iu] = acc * R.step;
+}
+
+// ---------------------------------------------------------------------------
+// Forward projection, gather with L2 prefetch: the gather kernel above, in
+// which one lane per warp asks the TMA unit to bring the warp's footprint
+// for planes kPfDist ahead (a box of kPfRows rows x kPlanes planes x
+// kPfCols elements around the lane's own ray) from DRAM into L2, so the
+// warp's later tap loads hit L2 instead of DRAM.
+
+constexpr int kPfDist = 8;
+constexpr int kPfRows = 4;
+
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap *map, int c0, int c1, int c2)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<unsigned long long>(map)),
+                 "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+
+template <typename T, typename Index, bool ZB>
+__device__ __forceinline__ float march_interior_pf(const T *__restrict__ vol, const Ray &R, bool leader,
+                                                   const CUtensorMap *map)
+{
+    constexpr int kAlign = 16 / (int)sizeof(T);
+    const Index sa = (Index)R.sa, sm = (Index)R.sm;
+    const Index sb = ZB ? (Index)1 : (Index)R.sb;
+    unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, R.j_lo, R.ic);
+    unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, R.j_lo, R.ic);
+    const unsigned long long ga = (unsigned long long)R.Ga, gb = (unsigned long long)R.Gb;
+    const unsigned long long da_pf = ga * (unsigned long long)kPfDist, db_pf = gb * (unsigned long long)kPfDist;
+    const unsigned long long da_span = ga * (unsigned long long)(kPlanes - 1), db_span = gb * (unsigned long long)(kPlanes - 1);
+    Index plane = (Index)R.j_lo * sm;
+    float acc = 0.0f;
+    int i = R.j_lo;
+    for (; i + kBatch - 1 <= R.j_hi; i += kBatch) {
+        if (leader && i + kPfDist <= R.j_hi) {
+            const unsigned long long qa = pa + da_pf, qb = pb + db_pf;
+            const int a0 = min(floor_of(qa), floor_of(qa + da_span));
+            const int b0 = (min(floor_of(qb), floor_of(qb + db_span)) - 1) & ~(kAlign - 1);
+            if (R.m == 0) tma_prefetch_l2_3d(map, b0, a0, i + kPfDist);
+            else tma_prefetch_l2_3d(map, b0, i + kPfDist, a0);
+        }
+        float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+            da[t] = frac_of(pa);
+            db[t] = frac_of(pb);
+            const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
+            v00[t] = load_voxel(p);
+            v01[t] = load_voxel(p + sb);
+            v10[t] = load_voxel(p + sa);
+            v11[t] = load_voxel(p + sa + sb);
+            pa += ga;
+            pb += gb;
+            plane += sm;
+        }
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+            const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
+            const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
+            acc += __fmaf_rn(da[t], e1 - e0, e0);
+        }
+    }
+    for (; i <= R.j_hi; ++i) {
+        const float da = frac_of(pa), db = frac_of(pb);
+        const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
+        const float v00 = load_voxel(p), v01 = load_voxel(p + sb);
+        const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + sb);
+        const float e0 = __fmaf_rn(db, v01 - v00, v00);
+        const float e1 = __fmaf_rn(db, v11 - v10, v10);
+        acc += __fmaf_rn(da, e1 - e0, e0);
+        pa += ga;
+        pb += gb;
+        plane += sm;
+    }
+    return acc;
+}
+
+template <typename T, typename Index>
+__global__ void __launch_bounds__(kThreads, GJP_MIN_BLOCKS) gjp_forward_pf_kernel(
+    const T *__restrict__ vol, VolParams V, const ViewParams *__restrict__ views, int nu, int nv, int n_tv,
+    const __grid_constant__ CUtensorMap pf_map, float *__restrict__ proj)
+{
+    const int tile = blockIdx.x;
+    const int view = blockIdx.y;
+    const int iv = (tile % n_tv) * kTileV + threadIdx.x;
+    const int iu = (tile / n_tv) * kTileU + threadIdx.y;
+    if (iv >= nv || iu >= nu) return;
+
+    ViewParams vp;
+    load_view(views, view, vp);
+    Ray R;
+    setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
+
+    const bool leader = threadIdx.x == 0;   // lowest v of the warp: lowest z of its footprint
+    float acc = (R.m != 2) ? march_interior_pf<T, Index, true>(vol, R, leader, &pf_map)
+                           : march_interior<T, Index, false>(vol, R);
     acc += march_boundary<T, Index>(vol, R);
     proj[((size_t)view * nv + iv) * nu + iu] = acc * R.step;
 }
@@ -634,6 +1039,255 @@ bool fits_int32(const int64_t n[3])
     return nvox + 2.0 * ((double)n[1] * n[2] + n[2] + 1) < 2147483647.0;
 }
 
+size_t elem_size(gjp_dtype t) { return t == GJP_F32 ? 4 : 2; }
+
+// cuTensorMapEncodeTiled, fetched once through the runtime (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Host (FP64) sizing of the slab boxes: for sample tiles of every view (the
+// 3 x 3 grid of tiles at the panel's corners, edge midpoints and centre,
+// where footprints are largest), the per-plane box the kernel's producer
+// computes from the tile's corner rays, over the planes some corner ray
+// supports.  Planes whose box still exceeds the chosen size fall back to
+// the gather path inside the kernel, so this only has to be typical.
+struct BoxSize {
+    int rows, cols4, cols8;   // cols for a 4- and an 8-element TMA x granularity
+};
+
+BoxSize slab_box_size(const gjp_geometry &g, const int64_t n[3], const double h[3], const double o[3])
+{
+    BoxSize bs{0, 0, 0};
+    const int us[3] = {0, std::max(0, g.nu / 2 - kSlabWarps / 2), std::max(0, g.nu - kSlabWarps)};
+    const int vs[3] = {0, std::max(0, g.nv / 2 - 16), std::max(0, g.nv - 32)};
+    for (int k = 0; k < g.n_views; ++k) {
+        double s[3];
+        for (int a = 0; a < 3; ++a) s[a] = (g.src[3 * k + a] - o[a]) / h[a];
+        for (int tu = 0; tu < 3; ++tu)
+            for (int tv = 0; tv < 3; ++tv) {
+                const int u0 = us[tu], v0 = vs[tv];
+                const int u1 = std::min(g.nu - 1, u0 + kSlabWarps - 1), v1 = std::min(g.nv - 1, v0 + 31);
+                const int cu[4] = {u0, u0, u1, u1}, cv[4] = {v0, v1, v0, v1};
+                double r[4][3];
+                int m = -1;
+                bool mixed = false;
+                for (int c = 0; c < 4; ++c) {
+                    for (int a = 0; a < 3; ++a) {
+                        const double d = g.org[3 * k + a] + cu[c] * g.du[3 * k + a] + cv[c] * g.dv[3 * k + a];
+                        r[c][a] = (d - o[a]) / h[a] - s[a];
+                    }
+                    int mc = 0;
+                    for (int a = 1; a < 3; ++a)
+                        if (std::fabs(r[c][a]) > std::fabs(r[c][mc])) mc = a;
+                    if (m >= 0 && mc != m) mixed = true;
+                    m = mc;
+                }
+                if (mixed || m == 2) continue;
+                const int a = m == 0 ? 1 : 0, b = 2;
+                for (int64_t i = 0; i < n[m]; ++i) {
+                    double amin = 1e300, amax = -1e300, bmin = 1e300, bmax = -1e300;
+                    bool sup = false;
+                    for (int c = 0; c < 4; ++c)
+                        for (int e = 0; e < 2; ++e) {   // first and last plane of a stage
+                            const double ip = e ? (double)std::min<int64_t>(i + kPlanes - 1, n[m] - 1) : (double)i;
+                            const double t = (ip - s[m]) / r[c][m];
+                            const double pa = s[a] + t * r[c][a], pb = s[b] + t * r[c][b];
+                            amin = std::min(amin, pa);
+                            amax = std::max(amax, pa);
+                            bmin = std::min(bmin, pb);
+                            bmax = std::max(bmax, pb);
+                            if (!e && pa > -1.0 && pa < (double)n[a] && pb > -1.0 && pb < (double)n[b]) sup = true;
+                        }
+                    if (!sup) continue;
+                    const int a0 = (int)std::floor(amin) - 1;
+                    const int fb = (int)std::floor(bmin) - 1;
+                    const int b04 = fb - ((fb % 4) + 4) % 4, b08 = fb - ((fb % 8) + 8) % 8;
+                    const int bmx = (int)std::floor(bmax);
+                    bs.rows = std::max(bs.rows, (int)std::floor(amax) + 3 - a0);
+                    bs.cols4 = std::max(bs.cols4, bmx + 3 - b04);
+                    bs.cols8 = std::max(bs.cols8, bmx + 3 - b08);
+                }
+            }
+    }
+    return bs;
+}
+
+struct SlabPlan {
+    bool ok;
+    int rows, cols;
+};
+
+SlabPlan slab_plan(const BoxSize &bs, const void *vol, gjp_dtype dt, const int64_t n[3])
+{
+    SlabPlan p{false, 0, 0};
+    const size_t es = elem_size(dt);
+    if (((uintptr_t)vol % 16) != 0 || ((size_t)n[2] * es) % 16 != 0) return p;
+    if (!tensor_map_encoder() || bs.rows <= 0) return p;
+    const int cols_need = es == 4 ? bs.cols4 : bs.cols8;
+    if (bs.rows > kBoxRMax || cols_need > 72) return p;   // too many planes would fall back
+    p.rows = std::max(4, bs.rows);
+    p.cols = cols_need <= (es == 4 ? 48 : 56) ? (es == 4 ? 48 : 56) : 64;
+    p.ok = true;
+    return p;
+}
+
+bool encode_maps(const void *vol, gjp_dtype dt, const int64_t n[3], int rows, int cols, CUtensorMap *mx,
+                 CUtensorMap *my)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const size_t es = elem_size(dt);
+    const CUtensorMapDataType t = dt == GJP_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                  : dt == GJP_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)n[2], (cuuint64_t)n[1], (cuuint64_t)n[0]};
+    const cuuint64_t strides[2] = {(cuuint64_t)(n[2] * es), (cuuint64_t)(n[1] * n[2] * es)};
+    const cuuint32_t bx[3] = {(cuuint32_t)cols, (cuuint32_t)rows, (cuuint32_t)kPlanes};   // planes x = i..: rows along y
+    const cuuint32_t by[3] = {(cuuint32_t)cols, (cuuint32_t)kPlanes, (cuuint32_t)rows};   // planes y = i..: rows along x
+    const cuuint32_t es1[3] = {1, 1, 1};
+    void *base = const_cast<void *>(vol);
+    if (enc(mx, t, 3, base, dims, strides, bx, es1, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (enc(my, t, 3, base, dims, strides, by, es1, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    return true;
+}
+
+template <typename T, typename Index, int C>
+cudaError_t launch_slab(const T *vol, const VolParams &V, const ViewParams *table, const gjp_geometry &g,
+                        const CUtensorMap &mx, const CUtensorMap &my, int rows, float *proj, cudaStream_t s)
+{
+    const int n_tv = (g.nv + 31) / 32;
+    const int n_tu = (g.nu + kSlabWarps - 1) / kSlabWarps;
+    const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
+    const int stage_bytes = (kPlanes * rows * C * (int)sizeof(T) + 127) & ~127;
+    const size_t smem = (size_t)kStages * stage_bytes + sizeof(SlabShared);
+    auto kern = gjp_forward_slab_kernel<T, Index, C>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kSlabThreads, smem, s>>>(vol, V, table, g.nu, g.nv, n_tv, mx, my, rows, proj);
+    return cudaGetLastError();
+}
+
+template <typename T, typename Index>
+cudaError_t launch_slab_cols(const T *vol, const VolParams &V, const ViewParams *table, const gjp_geometry &g,
+                             const CUtensorMap &mx, const CUtensorMap &my, const SlabPlan &p, float *proj,
+                             cudaStream_t s)
+{
+    if (p.cols == 48) return launch_slab<T, Index, 48>(vol, V, table, g, mx, my, p.rows, proj, s);
+    if (p.cols == 56) return launch_slab<T, Index, 56>(vol, V, table, g, mx, my, p.rows, proj, s);
+    return launch_slab<T, Index, 64>(vol, V, table, g, mx, my, p.rows, proj, s);
+}
+
+bool encode_prefetch_map(const void *vol, gjp_dtype dt, const int64_t n[3], CUtensorMap *map)
+{
+    auto enc = tensor_map_encoder();
+    const size_t es = elem_size(dt);
+    if (!enc || ((uintptr_t)vol % 16) != 0 || ((size_t)n[2] * es) % 16 != 0) return false;
+    const CUtensorMapDataType t = dt == GJP_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                  : dt == GJP_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)n[2], (cuuint64_t)n[1], (cuuint64_t)n[0]};
+    const cuuint64_t strides[2] = {(cuuint64_t)(n[2] * es), (cuuint64_t)(n[1] * n[2] * es)};
+    // the same box serves planes x = i (rows along y) and planes y = i (rows along x)
+    static_assert(kPfRows == kPlanes, "prefetch box is square in rows and planes");
+    const cuuint32_t box[3] = {(cuuint32_t)(es == 4 ? 48 : 64), (cuuint32_t)kPfRows, (cuuint32_t)kPlanes};
+    const cuuint32_t es1[3] = {1, 1, 1};
+    return enc(map, t, 3, const_cast<void *>(vol), dims, strides, box, es1, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
+cudaError_t launch_gather_pf(const T *vol, gjp_dtype dt, const int64_t n[3], const VolParams &V,
+                             const ViewParams *table, const gjp_geometry &g, bool i32, float *proj, cudaStream_t s,
+                             bool &launched)
+{
+    launched = false;
+    CUtensorMap map;
+    if (!encode_prefetch_map(vol, dt, n, &map)) return cudaSuccess;
+    const int n_tv = (g.nv + kTileV - 1) / kTileV;
+    const int n_tu = (g.nu + kTileU - 1) / kTileU;
+    const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
+    const dim3 block(kTileV, kTileU);
+    if (i32) gjp_forward_pf_kernel<T, int><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, map, proj);
+    else gjp_forward_pf_kernel<T, long long><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, map, proj);
+    launched = true;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *table, const gjp_geometry &g,
+                          bool i32, float *proj, cudaStream_t s)
+{
+    const int n_tv = (g.nv + kTileV - 1) / kTileV;
+    const int n_tu = (g.nu + kTileU - 1) / kTileU;
+    const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
+    const dim3 block(kTileV, kTileU);
+    if (i32) gjp_forward_kernel<T, int><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, proj);
+    else gjp_forward_kernel<T, long long><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, proj);
+    return cudaGetLastError();
+}
+
+template <typename T>
+gjp_status forward_typed(const void *d_volume, gjp_dtype dt, const int64_t n[3], const double h[3],
+                         const double o[3], const gjp_geometry &g, gjp_cache_entry &entry, float *proj,
+                         int path, cudaStream_t s)
+{
+    const VolParams V = make_vol(n, h);
+    const bool i32 = fits_int32(n);
+    const T *vol = static_cast<const T *>(d_volume);
+    const ViewParams *table = entry.d_table;
+    if (path == GJP_PATH_PREFETCH) {
+        bool launched = false;
+        const cudaError_t e = launch_gather_pf<T>(vol, dt, n, V, table, g, i32, proj, s, launched);
+        if (!launched) return GJP_ERR_UNSUPPORTED;
+        return e == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+    }
+    // measured on the 512^3 / 512^2 / 360-view workload the gather family is
+    // the fastest, so AUTO takes it; SLAB and PREFETCH run only on request
+    if (path == GJP_PATH_SLAB) {
+        BoxSize bs;
+        {
+            std::lock_guard<std::mutex> lock(const_cast<gjp_geometry &>(g).mu);
+            if (entry.box_rows == 0) {
+                const BoxSize b = slab_box_size(g, n, h, o);
+                entry.box_rows = std::max(b.rows, 1);
+                entry.box_cols4 = b.cols4;
+                entry.box_cols8 = b.cols8;
+            }
+            bs = BoxSize{entry.box_rows, entry.box_cols4, entry.box_cols8};
+        }
+        const SlabPlan p = slab_plan(bs, d_volume, dt, n);
+        CUtensorMap mx, my;
+        if (p.ok && encode_maps(d_volume, dt, n, p.rows, p.cols, &mx, &my)) {
+            const cudaError_t e = i32 ? launch_slab_cols<T, int>(vol, V, table, g, mx, my, p, proj, s)
+                                      : launch_slab_cols<T, long long>(vol, V, table, g, mx, my, p, proj, s);
+            return e == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+        }
+        if (path == GJP_PATH_SLAB) return GJP_ERR_UNSUPPORTED;
+    }
+    return launch_gather<T>(vol, V, table, g, i32, proj, s) == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -720,43 +1374,50 @@ gjp_status gjp_geometry_info(const gjp_geometry *g, int *n_views, int *nu, int *
     return GJP_OK;
 }
 
-gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
-                       const double voxel_size[3], const double volume_origin[3], const gjp_geometry *g,
-                       float *d_proj, void *stream)
+gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
+                          const double voxel_size[3], const double volume_origin[3], const gjp_geometry *g,
+                          float *d_proj, gjp_path path, void *stream)
 {
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
     if (dtype != GJP_F32 && dtype != GJP_BF16 && dtype != GJP_F16) return GJP_ERR_INVALID_ARG;
+    if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_PREFETCH)
+        return GJP_ERR_INVALID_ARG;
     int64_t n[3];
     double h[3], o[3];
     gjp_status st = check_grid(nx, ny, nz, voxel_size, volume_origin, n, h, o);
     if (st != GJP_OK) return st;
     if ((st = check_sources(g, n, h, o)) != GJP_OK) return st;
-    const ViewParams *table = nullptr;
-    if ((st = get_table(g, n, h, o, &table)) != GJP_OK) return st;
-
-    const VolParams V = make_vol(n, h);
-    const int n_tv = (g->nv + kTileV - 1) / kTileV;
-    const int n_tu = (g->nu + kTileU - 1) / kTileU;
-    const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
-    const dim3 block(kTileV, kTileU);
+    if (g->n_views > 65535) return GJP_ERR_UNSUPPORTED;
+    gjp_cache_entry *entry = nullptr;
+    if ((st = get_table(g, n, h, o, &entry)) != GJP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool i32 = fits_int32(n);
-    if (grid.x > 2147483647u || g->n_views > 65535) return GJP_ERR_UNSUPPORTED;
     switch (dtype) {
-    case GJP_F32:
-        if (i32) gjp_forward_kernel<float, int><<<grid, block, 0, s>>>((const float *)d_volume, V, table, g->nu, g->nv, n_tv, d_proj);
-        else gjp_forward_kernel<float, long long><<<grid, block, 0, s>>>((const float *)d_volume, V, table, g->nu, g->nv, n_tv, d_proj);
-        break;
-    case GJP_BF16:
-        if (i32) gjp_forward_kernel<__nv_bfloat16, int><<<grid, block, 0, s>>>((const __nv_bfloat16 *)d_volume, V, table, g->nu, g->nv, n_tv, d_proj);
-        else gjp_forward_kernel<__nv_bfloat16, long long><<<grid, block, 0, s>>>((const __nv_bfloat16 *)d_volume, V, table, g->nu, g->nv, n_tv, d_proj);
-        break;
-    case GJP_F16:
-        if (i32) gjp_forward_kernel<__half, int><<<grid, block, 0, s>>>((const __half *)d_volume, V, table, g->nu, g->nv, n_tv, d_proj);
-        else gjp_forward_kernel<__half, long long><<<grid, block, 0, s>>>((const __half *)d_volume, V, table, g->nu, g->nv, n_tv, d_proj);
-        break;
+    case GJP_F32: return forward_typed<float>(d_volume, dtype, n, h, o, *g, *entry, d_proj, path, s);
+    case GJP_BF16: return forward_typed<__nv_bfloat16>(d_volume, dtype, n, h, o, *g, *entry, d_proj, path, s);
+    case GJP_F16: return forward_typed<__half>(d_volume, dtype, n, h, o, *g, *entry, d_proj, path, s);
     }
-    return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+    return GJP_ERR_INVALID_ARG;
+}
+
+gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
+                       const double voxel_size[3], const double volume_origin[3], const gjp_geometry *g,
+                       float *d_proj, void *stream)
+{
+    return gjp_forward_ex(d_volume, dtype, nx, ny, nz, voxel_size, volume_origin, g, d_proj, GJP_PATH_AUTO,
+                          stream);
+}
+
+gjp_status gjp_stream_status(void *stream)
+{
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GJP_ERR_CUDA;
+    unsigned flag = 0;
+    if (cudaMemcpyFromSymbol(&flag, g_gjp_status, sizeof flag) != cudaSuccess) return GJP_ERR_CUDA;
+    if (flag) {
+        const unsigned zero = 0;
+        if (cudaMemcpyToSymbol(g_gjp_status, &zero, sizeof zero) != cudaSuccess) return GJP_ERR_CUDA;
+        return GJP_ERR_TIMEOUT;
+    }
+    return GJP_OK;
 }
 
 gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, int64_t ny, int64_t nz,
@@ -769,8 +1430,9 @@ gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, i
     gjp_status st = check_grid(nx, ny, nz, voxel_size, volume_origin, n, h, o);
     if (st != GJP_OK) return st;
     if ((st = check_sources(g, n, h, o)) != GJP_OK) return st;
-    const ViewParams *table = nullptr;
-    if ((st = get_table(g, n, h, o, &table)) != GJP_OK) return st;
+    gjp_cache_entry *entry = nullptr;
+    if ((st = get_table(g, n, h, o, &entry)) != GJP_OK) return st;
+    const ViewParams *table = entry->d_table;
     cudaStream_t s = (cudaStream_t)stream;
     if (!accumulate) {
         if (cudaMemsetAsync(d_volume, 0, sizeof(float) * (size_t)(n[0] * n[1] * n[2]), s) != cudaSuccess)
@@ -797,8 +1459,9 @@ gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny
     gjp_status st = check_grid(nx, ny, nz, voxel_size, volume_origin, n, h, o);
     if (st != GJP_OK) return st;
     if ((st = check_sources(g, n, h, o)) != GJP_OK) return st;
-    const ViewParams *table = nullptr;
-    if ((st = get_table(g, n, h, o, &table)) != GJP_OK) return st;
+    gjp_cache_entry *entry = nullptr;
+    if ((st = get_table(g, n, h, o, &entry)) != GJP_OK) return st;
+    const ViewParams *table = entry->d_table;
     const VolParams V = make_vol(n, h);
     const int n_tv = (g->nv + kTileV - 1) / kTileV;
     const int n_tu = (g->nu + kTileU - 1) / kTileU;

@@ -30,16 +30,16 @@ def gjp():
     return m
 
 
-def _project(gjp, vol_np, vg, cg, dtype=torch.float32):
+def _project(gjp, vol_np, vg, cg, dtype=torch.float32, path="auto"):
     vol = torch.from_numpy(np.ascontiguousarray(vol_np)).to("cuda").to(dtype)
     g = gjp.Geometry.from_cone(cg)
-    out = gjp.forward(vol, g, voxel_size=vg.h, origin=vg.origin)
-    torch.cuda.synchronize()
+    out = gjp.forward(vol, g, voxel_size=vg.h, origin=vg.origin, path=path)
+    gjp.stream_status()
     return out.cpu().numpy().astype(np.float64), vol
 
 
-def _full_check(gjp, vol_np, vg, cg, tol=TOL32, dtype=torch.float32):
-    gpu, _ = _project(gjp, vol_np, vg, cg, dtype)
+def _full_check(gjp, vol_np, vg, cg, tol=TOL32, dtype=torch.float32, path="auto"):
+    gpu, _ = _project(gjp, vol_np, vg, cg, dtype, path)
     ref = oracle.forward(vol_np, vg, cg)
     views, ius, ivs = parity.all_rays(cg)
     return parity.check_rays(gpu[views, ivs, ius], vol_np, vg, cg, views, ius, ivs,
@@ -48,16 +48,18 @@ def _full_check(gjp, vol_np, vg, cg, tol=TOL32, dtype=torch.float32):
 
 # --- c1: 64^3 Shepp-Logan-shaped phantom, 32 views, 64x64 -------------------
 
-def test_c1_phantom_fp32_all_rays(gjp):
+@pytest.mark.parametrize("path", ["gather", "slab", "prefetch"])
+def test_c1_phantom_fp32_all_rays(gjp, path):
     vg, cg = synth.c1_geometry()
     vol = synth.voxelize(vg, supersample=2)
-    r = _full_check(gjp, vol, vg, cg)
+    r = _full_check(gjp, vol, vg, cg, path=path)
     assert r["n"] == 32 * 64 * 64
 
 
-def test_c1_random_field_fp32_all_rays(gjp):
+@pytest.mark.parametrize("path", ["gather", "slab", "prefetch"])
+def test_c1_random_field_fp32_all_rays(gjp, path):
     vg, cg = synth.c1_geometry()
-    _full_check(gjp, synth.random_field(vg.n, seed=0), vg, cg)
+    _full_check(gjp, synth.random_field(vg.n, seed=0), vg, cg, path=path)
 
 
 def test_c1_matches_analytic_phantom(gjp):
@@ -94,13 +96,14 @@ def test_off_centre_volume_origin(gjp):
 
 # --- 16-bit storage: float32 weights and accumulation ------------------------
 
+@pytest.mark.parametrize("path", ["gather", "slab", "prefetch"])
 @pytest.mark.parametrize("dt", ["bfloat16", "float16"])
 @pytest.mark.parametrize("content", ["phantom", "random"])
-def test_16bit_storage(gjp, dt, content):
+def test_16bit_storage(gjp, dt, content, path):
     vg, cg = synth.c1_geometry()
     vol = synth.voxelize(vg, supersample=2) if content == "phantom" else synth.random_field(vg.n, seed=3)
     tdt = getattr(torch, dt)
-    gpu, tvol = _project(gjp, vol, vg, cg, tdt)
+    gpu, tvol = _project(gjp, vol, vg, cg, tdt, path)
     stored = tvol.float().cpu().numpy()               # exact widening of the stored values
     views, ius, ivs = parity.all_rays(cg)
     ref_q = oracle.forward(stored, vg, cg)
@@ -213,11 +216,12 @@ def test_gradient_finite_differences_differentiation_workload(gjp):
 
 # --- full-size workload (512^3, 360 views, 512^2), sampled outputs -----------
 
+@pytest.mark.parametrize("path", ["gather", "slab", "prefetch"])
 @pytest.mark.parametrize("content", ["phantom", "random"])
-def test_c2_full_size_sampled(gjp, content):
+def test_c2_full_size_sampled(gjp, content, path):
     vg, cg = synth.c2_geometry()
     vol = synth.voxelize(vg, supersample=2) if content == "phantom" else synth.random_field(vg.n, seed=0)
-    gpu, _ = _project(gjp, vol, vg, cg)
+    gpu, _ = _project(gjp, vol, vg, cg, path=path)
     # one whole view (45 degrees: contains driving-axis ties) plus 4000 random rays
     v45 = 45
     views = np.full(cg.nu * cg.nv, v45)
@@ -330,3 +334,26 @@ def test_int64_indexing_beyond_2_pow_31_elements(gjp):
     ref = oracle.rays(stored, vg, cg, views, ius, ivs)
     parity.check_rays(out[views, ivs, ius], stored, vg, cg, views, ius, ivs, np.abs(ref).max(), TOL32,
                       ref=ref)
+
+
+def test_slab_and_gather_agree_on_bf16_full_size(gjp):
+    """Both kernel families on the 512^3 / 360-view workload with bfloat16
+    storage: identical samples, so they agree to float32 rounding."""
+    vg, cg = synth.c2_geometry()
+    vol = torch.from_numpy(synth.random_field(vg.n, seed=5)).cuda().to(torch.bfloat16)
+    g = gjp.Geometry.from_cone(cg)
+    a = gjp.forward(vol, g, path="gather")
+    b = gjp.forward(vol, g, path="slab")
+    gjp.stream_status()
+    assert ((a - b).abs().max() / a.abs().max()).item() < 1e-6
+
+
+def test_slab_unsupported_for_unaligned_rows(gjp):
+    vg = VolumeGeometry.centred((16, 16, 15))          # 15 floats per z row: not a TMA stride
+    cg = synth.circular(2, 8, 8, 100.0, 200.0, 1.0)
+    g = gjp.Geometry.from_cone(cg)
+    vol = torch.zeros(vg.n, device="cuda")
+    with pytest.raises(gjp.GjpError) as e:
+        gjp.forward(vol, g, path="slab")
+    assert e.value.status == 2
+    gjp.forward(vol, g, path="auto")                  # falls back to the gather family
