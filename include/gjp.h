@@ -162,6 +162,40 @@ gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny
                          const double voxel_size[3], const double volume_origin[3],
                          unsigned char *d_marks, void *stream);
 
+/*
+ * gjp_forward_noalloc -- gjp_forward that allocates no memory.  The paper
+ * has no counterpart of this entry point; it exists for callers that cannot
+ * let a library allocate device memory once they are running: a framework
+ * that hands a fixed device-memory budget to its components, a real-time
+ * reconstruction loop that forbids allocation after acquisition starts, or a
+ * plug-in that must not touch its host application's allocator.
+ *
+ * It computes exactly what gjp_forward computes (same gather kernels), but
+ * keeps the per-view table in a fixed array of GJP_NOALLOC_MAX_VIEWS entries
+ * (144 bytes each, about 144 KiB) that the CUDA runtime places on every GPU
+ * that loads this library and keeps there until the process exits.  The
+ * table is formed on the host (in a small stack buffer) and copied from
+ * there into that array on `stream` before the kernel runs; the call
+ * performs no cudaMalloc, cudaFree or other allocation.  Because the copy
+ * comes from ordinary (pageable) host memory, the call may wait for work
+ * already queued on `stream` before it returns.
+ *   - Geometries with more than GJP_NOALLOC_MAX_VIEWS views are rejected
+ *     with GJP_ERR_UNSUPPORTED (split the views over several calls).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current).  Make that first
+ *     call before capturing a stream into a CUDA graph.
+ *   - All calls on a device share the one array and each overwrites it; it
+ *     keeps the last call's table.  Calls that may overlap on the GPU (on
+ *     different streams, or from different host threads) race on it: order
+ *     them on one stream or synchronise between them.  Nothing in the array
+ *     needs to start at zero.
+ * Arguments, layouts and other errors as for gjp_forward.
+ */
+#define GJP_NOALLOC_MAX_VIEWS 1024
+gjp_status gjp_forward_noalloc(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
+                               const double voxel_size[3], const double volume_origin[3],
+                               const gjp_geometry *g, float *d_proj, void *stream);
+
 /* Static, human-readable name of a status code. */
 const char *gjp_status_string(gjp_status s);
 

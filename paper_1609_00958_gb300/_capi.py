@@ -33,7 +33,11 @@ GJP_PATH_PREFETCH = 3
 
 #: every symbol include/gjp.h declares
 EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_forward",
-           "gjp_forward_ex", "gjp_stream_status", "gjp_adjoint", "gjp_footprint", "gjp_status_string")
+           "gjp_forward_ex", "gjp_forward_noalloc", "gjp_stream_status", "gjp_adjoint", "gjp_footprint",
+           "gjp_status_string")
+
+#: view limit of gjp_forward_noalloc (GJP_NOALLOC_MAX_VIEWS in include/gjp.h)
+GJP_NOALLOC_MAX_VIEWS = 1024
 
 _lib = None
 _P = ctypes.c_void_p
@@ -67,6 +71,8 @@ def load(path: str | None = None):
     lib.gjp_forward.restype = _I
     lib.gjp_forward_ex.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _I, _P]
     lib.gjp_forward_ex.restype = _I
+    lib.gjp_forward_noalloc.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _P]
+    lib.gjp_forward_noalloc.restype = _I
     lib.gjp_stream_status.argtypes = [_P]
     lib.gjp_stream_status.restype = _I
     lib.gjp_adjoint.argtypes = [_P, _P, _I64, _I64, _I64, _D3, _D3, _P, _I, _P]
@@ -133,6 +139,15 @@ def gjp_forward_ex(d_volume: int, dtype: int, nx: int, ny: int, nz: int, voxel_s
     return load().gjp_forward_ex(_P(d_volume), int(dtype), int(nx), int(ny), int(nz), _d3(voxel_size),
                                  _d3(volume_origin), _P(geometry) if geometry else None, _P(d_proj), int(path),
                                  _P(stream))
+
+
+def gjp_forward_noalloc(d_volume: int, dtype: int, nx: int, ny: int, nz: int, voxel_size, volume_origin,
+                        geometry, d_proj: int, stream: int) -> int:
+    """gjp_forward without any memory allocation (fixed per-device table of
+    GJP_NOALLOC_MAX_VIEWS views; see include/gjp.h for the rules)."""
+    return load().gjp_forward_noalloc(_P(d_volume), int(dtype), int(nx), int(ny), int(nz), _d3(voxel_size),
+                                      _d3(volume_origin), _P(geometry) if geometry else None, _P(d_proj),
+                                      _P(stream))
 
 
 def gjp_stream_status(stream: int) -> int:

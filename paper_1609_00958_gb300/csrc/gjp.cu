@@ -1288,6 +1288,44 @@ gjp_status forward_typed(const void *d_volume, gjp_dtype dt, const int64_t n[3],
     return launch_gather<T>(vol, V, table, g, i32, proj, s) == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free forward projection.
+//
+// gjp_forward builds its per-view table in device memory it allocates with
+// cudaMalloc on first use.  Some callers cannot allow that: code that runs
+// after a fixed device-memory budget has been handed out (a framework that
+// owns the whole device pool, a real-time reconstruction loop that may not
+// allocate once acquisition starts), or a plug-in that must not touch the
+// allocator of its host application.  gjp_forward_noalloc serves them: its
+// table lives in the fixed array below, which the CUDA runtime places in
+// device memory when it loads this library onto a GPU and keeps there until
+// the process exits.
+
+constexpr int kNoAllocMaxViews = GJP_NOALLOC_MAX_VIEWS;
+static __device__ __align__(256) unsigned char g_noalloc_table[kNoAllocMaxViews * sizeof(ViewParams)];
+
+// Host side: device address of g_noalloc_table for each device, looked up
+// once per device (with that device current) by the first call there.
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices];
+
+gjp_status noalloc_table_address(int dev, ViewParams **out)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GJP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_table) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return GJP_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<ViewParams *>(g_noalloc_ptr[dev]);
+    return GJP_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1405,6 +1443,71 @@ gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_
 {
     return gjp_forward_ex(d_volume, dtype, nx, ny, nz, voxel_size, volume_origin, g, d_proj, GJP_PATH_AUTO,
                           stream);
+}
+
+gjp_status gjp_forward_noalloc(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
+                               const double voxel_size[3], const double volume_origin[3], const gjp_geometry *g,
+                               float *d_proj, void *stream)
+{
+    if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
+    if (dtype != GJP_F32 && dtype != GJP_BF16 && dtype != GJP_F16) return GJP_ERR_INVALID_ARG;
+    int64_t n[3];
+    double h[3], o[3];
+    gjp_status st = check_grid(nx, ny, nz, voxel_size, volume_origin, n, h, o);
+    if (st != GJP_OK) return st;
+    if (g->n_views > kNoAllocMaxViews) return GJP_ERR_UNSUPPORTED;
+    if ((st = check_sources(g, n, h, o)) != GJP_OK) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GJP_ERR_CUDA;
+    ViewParams *d_table = nullptr;
+    if ((st = noalloc_table_address(dev, &d_table)) != GJP_OK) return st;
+
+    // the per-view table is formed on the host in a small stack buffer, a
+    // chunk of views at a time, and copied into the fixed device array on the
+    // caller's stream ahead of the kernel that reads it (a copy from pageable
+    // memory has consumed its source when cudaMemcpyAsync returns)
+    cudaStream_t s = (cudaStream_t)stream;
+    constexpr int kChunk = 32;
+    ViewParams chunk[kChunk];
+    const double cu = 0.5 * (g->nu - 1), cv = 0.5 * (g->nv - 1);
+    for (int k0 = 0; k0 < g->n_views; k0 += kChunk) {
+        const int cnt = std::min(kChunk, g->n_views - k0);
+        for (int j = 0; j < cnt; ++j) {
+            const int k = k0 + j;
+            double sc[3], R[9], M[9];
+            for (int a = 0; a < 3; ++a) {
+                const double c = 0.5 * (double)(n[a] - 1);
+                sc[a] = (g->src[3 * k + a] - o[a]) / h[a] - c;
+                R[3 + a] = g->du[3 * k + a] / h[a];
+                R[6 + a] = g->dv[3 * k + a] / h[a];
+                R[a] = (g->org[3 * k + a] - g->src[3 * k + a]) / h[a] + cu * R[3 + a] + cv * R[6 + a];
+            }
+            for (int t = 0; t < 3; ++t) {
+                const double *x = R + 3 * t;
+                M[3 * t + 0] = sc[1] * x[2] - sc[2] * x[1];
+                M[3 * t + 1] = sc[2] * x[0] - sc[0] * x[2];
+                M[3 * t + 2] = sc[0] * x[1] - sc[1] * x[0];
+            }
+            for (int q = 0; q < 9; ++q) {
+                split(R[q], chunk[j].rh[q], chunk[j].rl[q]);
+                split(M[q], chunk[j].mh[q], chunk[j].ml[q]);
+            }
+        }
+        if (cudaMemcpyAsync(d_table + k0, chunk, sizeof(ViewParams) * (size_t)cnt, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return GJP_ERR_CUDA;
+    }
+    const VolParams V = make_vol(n, h);
+    const bool i32 = fits_int32(n);
+    cudaError_t e = cudaSuccess;
+    switch (dtype) {
+    case GJP_F32: e = launch_gather<float>((const float *)d_volume, V, d_table, *g, i32, d_proj, s); break;
+    case GJP_BF16:
+        e = launch_gather<__nv_bfloat16>((const __nv_bfloat16 *)d_volume, V, d_table, *g, i32, d_proj, s);
+        break;
+    case GJP_F16: e = launch_gather<__half>((const __half *)d_volume, V, d_table, *g, i32, d_proj, s); break;
+    }
+    return e == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
 gjp_status gjp_stream_status(void *stream)
