@@ -219,22 +219,6 @@ def dist_setup(args):
     return rank, world, local
 
 
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
 def gpu_id_for_smi(local):
     import torch
     try:
@@ -251,6 +235,7 @@ def run_gjp(args):
     from paper_1609_00958_gb300 import build as libbuild
     libbuild.build()
     import paper_1609_00958_gb300 as gjp
+    from paper_1609_00958_gb300 import dist as gdist
 
     rank, world, local = dist_setup(args)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -296,7 +281,7 @@ def run_gjp(args):
     torch.cuda.synchronize()
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    barrier(world)
+    gdist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(gpu_id_for_smi(local)) as clk:
         t_start = torch.cuda.Event(enable_timing=True)
@@ -306,15 +291,15 @@ def run_gjp(args):
             step(evs[k])
         t_end.record(stream)
         torch.cuda.synchronize()
-    barrier(world)
+    gdist.barrier()
     clocks = clk.summary()
-    total_ms = t_start.elapsed_time(t_end)
-    total_ms = max_over_ranks(total_ms, world)
+    total_ms = gdist.max_over_ranks(t_start.elapsed_time(t_end))
     ms_per_step = total_ms / args.steps
     per_kernel_ms = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                      for i, n in enumerate(names)}
     samples_per_step = 3 * samples_per_kernel
-    value = samples_per_step * world / (ms_per_step * 1e-3) / 1e9
+    job_samples_per_step = gdist.sum_over_ranks(samples_per_step)     # every rank projects its own workload
+    value = job_samples_per_step / (ms_per_step * 1e-3) / 1e9
 
     hbm, peak_kind = peaks()
     kernels = {}
@@ -328,7 +313,7 @@ def run_gjp(args):
                                                  / (ms * 1e-3) / 1e9, 1)}
     dominant = max(names, key=lambda n: per_kernel_ms[n])
     kmap = {"forward_f32": "gjp_forward_kernel<float", "forward_bf16": "gjp_forward_kernel<__nv_bfloat16",
-            "adjoint_f32": "gjp_adjoint_kernel"}
+            "adjoint_f32": "gjp_adjoint_kernel<int"}
     traffic = dram_traffic(kmap[dominant])
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": kernels[dominant]["achieved_gbs"],
                 "peak": hbm, "peak_kind": peak_kind + " (copy, MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
@@ -337,7 +322,7 @@ def run_gjp(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, samples_per_step, world)
+        e2e = run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step)
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -361,10 +346,11 @@ def run_gjp(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, samples_per_step, world):
+def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step):
     """Same step through the public API with host buffers: pinned host
     volume in, projections and adjoint volume out, copies timed."""
     import torch
+    from paper_1609_00958_gb300 import dist as gdist
     h_vol32 = torch.from_numpy(vol_np).pin_memory()
     h_vol16 = h_vol32.to(torch.bfloat16).pin_memory()
     h_p32 = torch.empty(cg.n_views, cg.nv, cg.nu).pin_memory()
@@ -389,16 +375,15 @@ def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, samples_per_step, worl
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize()
-    barrier(world)
+    gdist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
         torch.cuda.synchronize()      # the host reads the step's results
-    wall = time.perf_counter() - t0
-    wall = max_over_ranks(wall, world)
+    wall = gdist.max_over_ranks(time.perf_counter() - t0)
     bi = h_vol32.numel() * 4 + h_vol16.numel() * 2
     bo = (h_p32.numel() + h_p16.numel() + h_back.numel()) * 4
-    return {"value": round(samples_per_step * world / (wall / args.steps) / 1e9, 3), "unit": UNIT,
+    return {"value": round(job_samples_per_step / (wall / args.steps) / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
             "ms_per_step": round(1e3 * wall / args.steps, 3)}
 
