@@ -150,6 +150,21 @@ gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, i
                        float *d_volume, int accumulate, void *stream);
 
 /*
+ * gjp_adjoint_ex -- gjp_adjoint with an explicit kernel family:
+ * GJP_PATH_GATHER scatters every tap with a float32 atomic addition to
+ * global memory; GJP_PATH_SLAB accumulates each detector tile's taps for a
+ * few planes in shared memory and adds the whole box to the volume with one
+ * TMA bulk tensor reduction (same volume alignment conditions as the slab
+ * forward; tiles with mixed driving axes fall back to the scatter);
+ * GJP_PATH_AUTO takes SLAB where it applies, else GATHER.  GJP_PATH_PREFETCH
+ * is not an adjoint family (GJP_ERR_INVALID_ARG).  Results agree to float32
+ * rounding; neither is bitwise deterministic.
+ */
+gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx, int64_t ny,
+                          int64_t nz, const double voxel_size[3], const double volume_origin[3],
+                          float *d_volume, int accumulate, gjp_path path, void *stream);
+
+/*
  * gjp_footprint -- measurement helper (not part of the method): sets
  * d_marks[voxel] = 1 for every voxel that receives a non-zero
  * interpolation weight from some ray of view `view` (the view's compulsory

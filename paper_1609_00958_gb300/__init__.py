@@ -111,9 +111,11 @@ def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None,
 
 
 def adjoint(proj, geometry: Geometry, shape, voxel_size=(1.0, 1.0, 1.0), origin=None, out=None,
-            accumulate: bool = False, stream=None):
+            accumulate: bool = False, stream=None, path: str = "auto"):
     """Matched transpose of :func:`forward`: ``A^T proj`` as a float32
-    ``shape`` volume (added into ``out`` when ``accumulate``)."""
+    ``shape`` volume (added into ``out`` when ``accumulate``).  ``path`` is
+    "auto", "gather" (global atomics) or "slab" (shared-memory boxes with
+    TMA bulk reduction)."""
     torch = _torch()
     _check_cuda(proj, "proj")
     if proj.dtype != torch.float32 or tuple(proj.shape) != geometry.proj_shape:
@@ -125,8 +127,8 @@ def adjoint(proj, geometry: Geometry, shape, voxel_size=(1.0, 1.0, 1.0), origin=
     if out.dtype != torch.float32 or tuple(out.shape) != shape or out.device != proj.device:
         raise ValueError("out must be a float32 volume of the given shape on proj's device")
     with torch.cuda.device(proj.device):
-        st = _capi.gjp_adjoint(proj.data_ptr(), geometry.handle, *shape, voxel_size, origin, out.data_ptr(),
-                               1 if accumulate else 0, _stream(proj, stream))
+        st = _capi.gjp_adjoint_ex(proj.data_ptr(), geometry.handle, *shape, voxel_size, origin, out.data_ptr(),
+                                  1 if accumulate else 0, _PATHS[path], _stream(proj, stream))
     if st != _capi.GJP_OK:
         raise GjpError(st, "gjp_adjoint")
     return out

@@ -33,8 +33,8 @@ GJP_PATH_PREFETCH = 3
 
 #: every symbol include/gjp.h declares
 EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_forward",
-           "gjp_forward_ex", "gjp_forward_noalloc", "gjp_stream_status", "gjp_adjoint", "gjp_footprint",
-           "gjp_status_string")
+           "gjp_forward_ex", "gjp_forward_noalloc", "gjp_stream_status", "gjp_adjoint", "gjp_adjoint_ex",
+           "gjp_footprint", "gjp_status_string")
 
 #: view limit of gjp_forward_noalloc (GJP_NOALLOC_MAX_VIEWS in include/gjp.h)
 GJP_NOALLOC_MAX_VIEWS = 1024
@@ -77,6 +77,8 @@ def load(path: str | None = None):
     lib.gjp_stream_status.restype = _I
     lib.gjp_adjoint.argtypes = [_P, _P, _I64, _I64, _I64, _D3, _D3, _P, _I, _P]
     lib.gjp_adjoint.restype = _I
+    lib.gjp_adjoint_ex.argtypes = [_P, _P, _I64, _I64, _I64, _D3, _D3, _P, _I, _I, _P]
+    lib.gjp_adjoint_ex.restype = _I
     lib.gjp_footprint.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P]
     lib.gjp_footprint.restype = _I
     lib.gjp_status_string.argtypes = [_I]
@@ -159,6 +161,13 @@ def gjp_adjoint(d_proj: int, geometry, nx: int, ny: int, nz: int, voxel_size, vo
     return load().gjp_adjoint(_P(d_proj), _P(geometry) if geometry else None, int(nx), int(ny), int(nz),
                               _d3(voxel_size), _d3(volume_origin), _P(d_volume), int(accumulate),
                               _P(stream))
+
+
+def gjp_adjoint_ex(d_proj: int, geometry, nx: int, ny: int, nz: int, voxel_size, volume_origin,
+                   d_volume: int, accumulate: int, path: int, stream: int) -> int:
+    return load().gjp_adjoint_ex(_P(d_proj), _P(geometry) if geometry else None, int(nx), int(ny), int(nz),
+                                 _d3(voxel_size), _d3(volume_origin), _P(d_volume), int(accumulate), int(path),
+                                 _P(stream))
 
 
 def gjp_footprint(geometry, view: int, nx: int, ny: int, nz: int, voxel_size, volume_origin,

@@ -895,26 +895,11 @@ __global__ void __launch_bounds__(kThreads, GJP_MIN_BLOCKS) gjp_forward_pf_kerne
 // ---------------------------------------------------------------------------
 // Adjoint: the same (ray, plane, tap) triples scatter y * step * weight.
 
+// Scatter of one ray over all its planes with global float atomics.
 template <typename Index>
-__global__ void __launch_bounds__(kThreads) gjp_adjoint_kernel(
-    const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views,
-    int nu, int nv, int n_tv, float *__restrict__ vol)
+__device__ __forceinline__ void scatter_ray(const Ray &R, float ys, float *__restrict__ vol)
 {
-    const int tile = blockIdx.x;
-    const int view = blockIdx.y;
-    const int iv = (tile % n_tv) * kTileV + threadIdx.x;
-    const int iu = (tile / n_tv) * kTileU + threadIdx.y;
-    if (iv >= nv || iu >= nu) return;
-    const float y = __ldg(proj + ((size_t)view * nv + iv) * nu + iu);
-    if (y == 0.0f) return;   // contributes exactly nothing
-
-    ViewParams vp;
-    load_view(views, view, vp);
-    Ray R;
-    setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
-    const float ys = y * R.step;
     const Index sa = (Index)R.sa, sb = (Index)R.sb, sm = (Index)R.sm;
-
     // interior planes
     unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, R.j_lo, R.ic);
     unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, R.j_lo, R.ic);
@@ -950,6 +935,220 @@ __global__ void __launch_bounds__(kThreads) gjp_adjoint_kernel(
         if (a1 && b0) atomicAdd(p + sa, w1 * (1.0f - db));
         if (a1 && b1) atomicAdd(p + sa + sb, w1 * db);
     }
+}
+
+template <typename Index>
+__global__ void __launch_bounds__(kThreads) gjp_adjoint_kernel(
+    const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views,
+    int nu, int nv, int n_tv, float *__restrict__ vol)
+{
+    const int tile = blockIdx.x;
+    const int view = blockIdx.y;
+    const int iv = (tile % n_tv) * kTileV + threadIdx.x;
+    const int iu = (tile / n_tv) * kTileU + threadIdx.y;
+    if (iv >= nv || iu >= nu) return;
+    const float y = __ldg(proj + ((size_t)view * nv + iv) * nu + iu);
+    if (y == 0.0f) return;   // contributes exactly nothing
+
+    ViewParams vp;
+    load_view(views, view, vp);
+    Ray R;
+    setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
+    scatter_ray<Index>(R, y * R.step, vol);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint, shared-memory slab with TMA bulk reduction.
+//
+// The transpose of the slab forward: a block of kSlabWarps detector
+// columns x 32 rows sweeps its planes kPlanes at a time; each stage's
+// contributions are accumulated into a zeroed shared-memory box (the same
+// box the forward would load) with shared-memory atomics, and one
+// cp.reduce.async.bulk.tensor adds the whole box to the volume in L2.
+// This replaces four scattered global reductions per sample by bulk
+// sector-wide reductions.  Reductions may not start at a negative
+// coordinate, so box origins are clamped to >= 0; taps below index 0 lie
+// outside the volume and are skipped, and the TMA unit drops box elements
+// beyond the volume.
+
+constexpr int kAdjSlots = 2;
+
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap *map, const void *src, int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3, %4}], [%1];"
+        ::"l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_addr(src)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int N> __device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+template <int N> __device__ __forceinline__ void bulk_wait()
+{
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+struct AdjShared {
+    int4 hdr[kAdjSlots];            // a0, b0 (clamped to >= 0), box fits, unused
+    long long corner[4][4];
+    int sweep_lo, sweep_hi, m_first, mixed;
+};
+
+template <typename Index, int kBoxC>
+__global__ void __launch_bounds__(kSlabWarps * 32, 3) gjp_adjoint_slab_kernel(
+    const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views, int nu, int nv, int n_tv,
+    const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y, int box_r,
+    float *__restrict__ vol)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int stage_elems = kPlanes * box_r * kBoxC;
+    const int stage_bytes = (stage_elems * 4 + 127) & ~127;
+    AdjShared &S = *reinterpret_cast<AdjShared *>(smem_raw + kAdjSlots * stage_bytes);
+    float *boxes = reinterpret_cast<float *>(smem_raw);
+    const int stage_stride = stage_bytes / 4;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x, view = blockIdx.y;
+    const int v_base = (tile % n_tv) * 32, u_base = (tile / n_tv) * kSlabWarps;
+    const int iv = v_base + lane, iu = u_base + warp;
+    const bool have_ray = iv < nv && iu < nu;
+
+    if (tid == 0) {
+        S.sweep_lo = 0x7fffffff;
+        S.sweep_hi = -1;
+        S.m_first = -1;
+        S.mixed = 0;
+    }
+    __syncthreads();
+    Ray R;
+    float ys = 0.0f;
+    if (have_ray) {
+        ViewParams vp;
+        load_view(views, view, vp);
+        setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
+        ys = __ldg(proj + ((size_t)view * nv + iv) * nu + iu) * R.step;
+        if (R.s_lo <= R.s_hi && ys != 0.0f) {
+            atomicMin(&S.sweep_lo, R.s_lo);
+            atomicMax(&S.sweep_hi, R.s_hi);
+        }
+        atomicCAS(&S.m_first, -1, R.m);
+    }
+    __syncthreads();
+    if (have_ray) {
+        if (R.m != S.m_first) S.mixed = 1;
+        const int u_last = min(kSlabWarps, nu - u_base) - 1, v_last = min(32, nv - v_base) - 1;
+        for (int cu = 0; cu < 2; ++cu)
+            for (int cv = 0; cv < 2; ++cv)
+                if ((cu == 0 ? warp == 0 : warp == u_last) && (cv == 0 ? lane == 0 : lane == v_last)) {
+                    long long *c = S.corner[2 * cu + cv];
+                    c[0] = R.Pa;
+                    c[1] = R.Ga;
+                    c[2] = R.Pb;
+                    c[3] = R.Gb;
+                }
+    }
+    __syncthreads();
+    const int m = S.m_first;
+    if (S.mixed || m < 0 || m == 2) {       // global-atomic scatter for the whole tile
+        if (have_ray && ys != 0.0f) scatter_ray<Index>(R, ys, vol);
+        return;
+    }
+    const int I0 = S.sweep_lo, I1 = S.sweep_hi;
+    const int n_stages = I1 >= I0 ? (I1 - I0) / kPlanes + 1 : 0;
+    const int row_stride = m == 0 ? kBoxC : kPlanes * kBoxC;
+    const int plane_stride = m == 0 ? box_r * kBoxC : kBoxC;
+    const int nm = V.n[m];
+    const int ic = (nm - 1) >> 1;
+    const unsigned na = have_ray ? (unsigned)R.na : 0u, nb = have_ray ? (unsigned)R.nb : 0u;
+    const Index sa = have_ray ? (Index)R.sa : 0, sb = have_ray ? (Index)R.sb : 0, sm = have_ray ? (Index)R.sm : 0;
+    unsigned long long pa = 0, pb = 0, ga = 0, gb = 0;
+    int s_lo = 1, s_hi = 0;
+    if (have_ray && ys != 0.0f) {
+        pa = (unsigned long long)pos_at(R.Pa, R.Ga, I0, R.ic);
+        pb = (unsigned long long)pos_at(R.Pb, R.Gb, I0, R.ic);
+        ga = (unsigned long long)R.Ga;
+        gb = (unsigned long long)R.Gb;
+        s_lo = R.s_lo;
+        s_hi = R.s_hi;
+    }
+    // corner tracked by this lane of warp 0 (stage box from the corners at
+    // the stage's first and last plane, as in the forward)
+    const long long *cr = S.corner[lane & 3];
+    const long long cPa = cr[0], cGa = cr[1], cPb = cr[2], cGb = cr[3];
+    const int cend = (lane >> 2) & 1;
+
+    for (int st = 0; st < n_stages; ++st) {
+        const int slot = st & (kAdjSlots - 1);
+        float *box = boxes + slot * stage_stride;
+        const int i0 = I0 + st * kPlanes;
+        if (warp == 0) {
+            const int i = cend ? min(i0 + kPlanes - 1, I1) : i0;
+            const int fa = floor_of((unsigned long long)pos_at(cPa, cGa, i, ic));
+            const int fb = floor_of((unsigned long long)pos_at(cPb, cGb, i, ic));
+            const int amin = __reduce_min_sync(0xffffffffu, fa), amax = __reduce_max_sync(0xffffffffu, fa);
+            const int bmin = __reduce_min_sync(0xffffffffu, fb), bmax = __reduce_max_sync(0xffffffffu, fb);
+            if (lane == 0) {
+                const int a0 = amin - 1;
+                const int b0 = (bmin - 1) & ~3;
+                const bool fits = (amax + 3 - a0 <= box_r) && (bmax + 3 - b0 <= kBoxC);
+                S.hdr[slot] = make_int4(max(a0, 0), max(b0, 0), fits ? 1 : 0, 0);
+                // the reduction issued kAdjSlots stages ago from this slot must
+                // have finished reading it before it is zeroed again
+                bulk_wait_read<kAdjSlots - 1>();
+            }
+        }
+        __syncthreads();                                    // header visible, slot free
+        const int4 h = S.hdr[slot];
+        if (h.z) {
+            float4 *b4 = reinterpret_cast<float4 *>(box);
+            for (int k = tid; k < stage_elems / 4; k += kSlabWarps * 32) b4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();                                    // box zeroed
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const int i = i0 + p;
+            if (i >= s_lo && i <= s_hi) {
+                const float da = frac_of(pa), db = frac_of(pb);
+                const int ia = floor_of(pa), ib = floor_of(pb);
+                const float w0 = (1.0f - da) * ys, w1 = da * ys;
+                const float w00 = w0 * (1.0f - db), w01 = w0 * db, w10 = w1 * (1.0f - db), w11 = w1 * db;
+                if (h.z) {
+                    const int r = ia - h.x, c = ib - h.y;   // r, c >= -1; -1 only outside the volume
+                    float *q = box + (r * row_stride + c + p * plane_stride);
+                    const bool r0 = r >= 0, c0 = c >= 0;
+                    if (r0 && c0) atomicAdd(q, w00);
+                    if (r0) atomicAdd(q + 1, w01);
+                    if (c0) atomicAdd(q + row_stride, w10);
+                    atomicAdd(q + row_stride + 1, w11);
+                } else {
+                    const bool a0 = (unsigned)ia < na, a1 = (unsigned)(ia + 1) < na;
+                    const bool b0 = (unsigned)ib < nb, b1 = (unsigned)(ib + 1) < nb;
+                    float *q = vol + ((Index)i * sm + (Index)ia * sa + (Index)ib * sb);
+                    if (a0 && b0) atomicAdd(q, w00);
+                    if (a0 && b1) atomicAdd(q + sb, w01);
+                    if (a1 && b0) atomicAdd(q + sa, w10);
+                    if (a1 && b1) atomicAdd(q + sa + sb, w11);
+                }
+            }
+            pa += ga;
+            pb += gb;
+        }
+        fence_proxy_async_smem();                           // box writes -> async proxy
+        __syncthreads();                                    // box complete
+        if (tid == 0 && h.z) {
+            if (m == 0) tma_reduce_add_3d(&map_x, box, h.y, h.x, i0);     // planes x = i0 ..
+            else tma_reduce_add_3d(&map_y, box, h.y, i0, h.x);            // planes y = i0 ..
+            bulk_commit();
+        }
+    }
+    if (tid == 0) bulk_wait<0>();
 }
 
 // Marks every voxel that receives a non-zero interpolation weight from a
@@ -1288,6 +1487,54 @@ gjp_status forward_typed(const void *d_volume, gjp_dtype dt, const int64_t n[3],
     return launch_gather<T>(vol, V, table, g, i32, proj, s) == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
+template <typename Index, int C>
+cudaError_t launch_adjoint_slab(const float *proj, const VolParams &V, const ViewParams *table,
+                                const gjp_geometry &g, const CUtensorMap &mx, const CUtensorMap &my, int rows,
+                                float *vol, cudaStream_t s)
+{
+    const int n_tv = (g.nv + 31) / 32;
+    const int n_tu = (g.nu + kSlabWarps - 1) / kSlabWarps;
+    const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
+    const int stage_bytes = (kPlanes * rows * C * 4 + 127) & ~127;
+    const size_t smem = (size_t)kAdjSlots * stage_bytes + sizeof(AdjShared);
+    auto kern = gjp_adjoint_slab_kernel<Index, C>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kSlabWarps * 32, smem, s>>>(proj, V, table, g.nu, g.nv, n_tv, mx, my, rows, vol);
+    return cudaGetLastError();
+}
+
+// Slab adjoint when its conditions hold; returns false (nothing launched) otherwise.
+bool try_adjoint_slab(const float *proj, const int64_t n[3], const double h[3], const double o[3],
+                      const gjp_geometry &g, gjp_cache_entry &entry, float *vol, cudaStream_t s, cudaError_t &err)
+{
+    BoxSize bs;
+    {
+        std::lock_guard<std::mutex> lock(const_cast<gjp_geometry &>(g).mu);
+        if (entry.box_rows == 0) {
+            const BoxSize b = slab_box_size(g, n, h, o);
+            entry.box_rows = std::max(b.rows, 1);
+            entry.box_cols4 = b.cols4;
+            entry.box_cols8 = b.cols8;
+        }
+        bs = BoxSize{entry.box_rows, entry.box_cols4, entry.box_cols8};
+    }
+    const SlabPlan p = slab_plan(bs, vol, GJP_F32, n);
+    CUtensorMap mx, my;
+    if (!p.ok || !encode_maps(vol, GJP_F32, n, p.rows, p.cols, &mx, &my)) return false;
+    const VolParams V = make_vol(n, h);
+    const bool i32 = fits_int32(n);
+    if (p.cols == 48)
+        err = i32 ? launch_adjoint_slab<int, 48>(proj, V, entry.d_table, g, mx, my, p.rows, vol, s)
+                  : launch_adjoint_slab<long long, 48>(proj, V, entry.d_table, g, mx, my, p.rows, vol, s);
+    else
+        err = i32 ? launch_adjoint_slab<int, 64>(proj, V, entry.d_table, g, mx, my, p.rows, vol, s)
+                  : launch_adjoint_slab<long long, 64>(proj, V, entry.d_table, g, mx, my, p.rows, vol, s);
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free forward projection.
 //
@@ -1523,16 +1770,18 @@ gjp_status gjp_stream_status(void *stream)
     return GJP_OK;
 }
 
-gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, int64_t ny, int64_t nz,
-                       const double voxel_size[3], const double volume_origin[3], float *d_volume,
-                       int accumulate, void *stream)
+gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx, int64_t ny, int64_t nz,
+                          const double voxel_size[3], const double volume_origin[3], float *d_volume,
+                          int accumulate, gjp_path path, void *stream)
 {
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
+    if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB) return GJP_ERR_INVALID_ARG;
     int64_t n[3];
     double h[3], o[3];
     gjp_status st = check_grid(nx, ny, nz, voxel_size, volume_origin, n, h, o);
     if (st != GJP_OK) return st;
     if ((st = check_sources(g, n, h, o)) != GJP_OK) return st;
+    if (g->n_views > 65535) return GJP_ERR_UNSUPPORTED;
     gjp_cache_entry *entry = nullptr;
     if ((st = get_table(g, n, h, o, &entry)) != GJP_OK) return st;
     const ViewParams *table = entry->d_table;
@@ -1541,15 +1790,28 @@ gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, i
         if (cudaMemsetAsync(d_volume, 0, sizeof(float) * (size_t)(n[0] * n[1] * n[2]), s) != cudaSuccess)
             return GJP_ERR_CUDA;
     }
+    if (path != GJP_PATH_GATHER) {
+        cudaError_t e = cudaSuccess;
+        if (try_adjoint_slab(d_proj, n, h, o, *g, *entry, d_volume, s, e))
+            return e == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+        if (path == GJP_PATH_SLAB) return GJP_ERR_UNSUPPORTED;
+    }
     const VolParams V = make_vol(n, h);
     const int n_tv = (g->nv + kTileV - 1) / kTileV;
     const int n_tu = (g->nu + kTileU - 1) / kTileU;
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
     const dim3 block(kTileV, kTileU);
-    if (g->n_views > 65535) return GJP_ERR_UNSUPPORTED;
     if (fits_int32(n)) gjp_adjoint_kernel<int><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, d_volume);
     else gjp_adjoint_kernel<long long><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, d_volume);
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+}
+
+gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, int64_t ny, int64_t nz,
+                       const double voxel_size[3], const double volume_origin[3], float *d_volume,
+                       int accumulate, void *stream)
+{
+    return gjp_adjoint_ex(d_proj, g, nx, ny, nz, voxel_size, volume_origin, d_volume, accumulate, GJP_PATH_AUTO,
+                          stream);
 }
 
 gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny, int64_t nz,
