@@ -83,6 +83,18 @@ gjp_status gjp_geometry_create(int n_views, int nu, int nv, const double *src,
  * freed with cudaFree, which waits for work that may still use them. */
 void gjp_geometry_destroy(gjp_geometry *g);
 
+/* Interpolation weight function w(d) of Eq. 9-12: GJP_WEIGHT_LIN is
+ * w_lin(d) = 1 - d (Eq. 13, multilinear, the default); GJP_WEIGHT_SPL is
+ * w_spl(d) = 1 - 3d^2 + 2d^3 (Eq. 14, C1 at the grid points). */
+typedef enum { GJP_WEIGHT_LIN = 0, GJP_WEIGHT_SPL = 1 } gjp_weight;
+
+/* Selects the weight function used by every later projection with g
+ * (forward and adjoint alike, so the pair stays transposed).  The GATHER
+ * families support both weights; SLAB and PREFETCH implement w_lin only and
+ * return GJP_ERR_UNSUPPORTED when asked for with w_spl (AUTO then uses
+ * GATHER).  Returns GJP_ERR_INVALID_ARG for NULL or an unknown weight. */
+gjp_status gjp_geometry_set_weight(gjp_geometry *g, gjp_weight w);
+
 /* Reads back the detector shape of a geometry.  Any output pointer may be NULL. */
 gjp_status gjp_geometry_info(const gjp_geometry *g, int *n_views, int *nu, int *nv);
 

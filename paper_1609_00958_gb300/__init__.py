@@ -27,7 +27,7 @@ class Geometry:
     """Owns a ``gjp_geometry`` handle (host copy of the per-view source and
     detector frames; device tables are built on first use per device)."""
 
-    def __init__(self, src, det_origin, det_u, det_v, nu: int, nv: int):
+    def __init__(self, src, det_origin, det_u, det_v, nu: int, nv: int, weight: str = "lin"):
         src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 3)
         self.n_views = int(src.shape[0])
         self.nu, self.nv = int(nu), int(nv)
@@ -35,11 +35,22 @@ class Geometry:
         if st != _capi.GJP_OK:
             raise GjpError(st, "gjp_geometry_create")
         self.handle = h
+        self.weight = "lin"
+        if weight != "lin":
+            self.set_weight(weight)
 
     @classmethod
-    def from_cone(cls, cg) -> "Geometry":
+    def from_cone(cls, cg, weight: str = "lin") -> "Geometry":
         """From any object with ``src, det_origin, det_u, det_v, nu, nv``."""
-        return cls(cg.src, cg.det_origin, cg.det_u, cg.det_v, cg.nu, cg.nv)
+        return cls(cg.src, cg.det_origin, cg.det_u, cg.det_v, cg.nu, cg.nv, weight=weight)
+
+    def set_weight(self, weight: str):
+        """Interpolation weight: "lin" (w_lin, Eq. 13) or "spl" (w_spl, Eq. 14)."""
+        code = {"lin": _capi.GJP_WEIGHT_LIN, "spl": _capi.GJP_WEIGHT_SPL}[weight]
+        st = _capi.gjp_geometry_set_weight(self.handle, code)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_geometry_set_weight")
+        self.weight = weight
 
     def close(self):
         h, self.handle = getattr(self, "handle", None), None

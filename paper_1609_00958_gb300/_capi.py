@@ -26,13 +26,17 @@ GJP_F32 = 0
 GJP_BF16 = 1
 GJP_F16 = 2
 
+GJP_WEIGHT_LIN = 0
+GJP_WEIGHT_SPL = 1
+
 GJP_PATH_AUTO = 0
 GJP_PATH_GATHER = 1
 GJP_PATH_SLAB = 2
 GJP_PATH_PREFETCH = 3
 
 #: every symbol include/gjp.h declares
-EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_forward",
+EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_geometry_set_weight",
+           "gjp_forward",
            "gjp_forward_ex", "gjp_forward_noalloc", "gjp_stream_status", "gjp_adjoint", "gjp_adjoint_ex",
            "gjp_footprint", "gjp_status_string")
 
@@ -67,6 +71,8 @@ def load(path: str | None = None):
     lib.gjp_geometry_destroy.restype = None
     lib.gjp_geometry_info.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
     lib.gjp_geometry_info.restype = _I
+    lib.gjp_geometry_set_weight.argtypes = [_P, _I]
+    lib.gjp_geometry_set_weight.restype = _I
     lib.gjp_forward.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _P]
     lib.gjp_forward.restype = _I
     lib.gjp_forward_ex.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _I, _P]
@@ -127,6 +133,10 @@ def gjp_geometry_info(handle):
     st = load().gjp_geometry_info(_P(handle) if handle else None, ctypes.byref(a), ctypes.byref(b),
                                   ctypes.byref(c))
     return st, a.value, b.value, c.value
+
+
+def gjp_geometry_set_weight(handle, weight: int) -> int:
+    return load().gjp_geometry_set_weight(_P(handle) if handle else None, int(weight))
 
 
 def gjp_forward(d_volume: int, dtype: int, nx: int, ny: int, nz: int, voxel_size, volume_origin,

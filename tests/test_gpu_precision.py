@@ -1,0 +1,76 @@
+"""Precision form: large Shepp-Logan-shaped volumes stored in float32,
+bfloat16 and float16 (float32 weights and accumulation), projected on the
+1024^3 / 1024^2 / 720-view and 2048^3 / 2048^2 / 64-view workloads.
+
+Errors are measured against the FP64 oracle evaluated on the unquantised
+float32 volume, on sampled rays of an evenly spaced subset of (at most) 128
+views: max error relative to the largest reference value (bound 1e-5 for
+float32 storage, 5e-3 for 16-bit storage) and RMS error.  With
+GJP_REPORT_DIR set, the error table is written there as JSON.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BOUND = {"float32": 1e-5, "bfloat16": 5e-3, "float16": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def gjp():
+    from paper_1609_00958_gb300 import build
+    build.build()
+    import paper_1609_00958_gb300 as m
+    return m
+
+
+def _host_gb():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2 ** 30
+    except (ValueError, OSError):
+        return 0.0
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_precision_form(gjp, n):
+    vol_gb = n ** 3 * 4 / 2 ** 30
+    free, _ = torch.cuda.mem_get_info()
+    if free < 2.2 * vol_gb * 2 ** 30 or _host_gb() < 2.5 * vol_gb:
+        pytest.skip("not enough device or host memory for this size")
+    vg, cg_all = synth.c3_geometry(n)
+    views = np.unique(np.linspace(0, cg_all.n_views - 1, min(128, cg_all.n_views)).round().astype(int))
+    cg = cg_all.subset(views)
+    vol = synth.voxelize(vg, supersample=2 if n <= 1024 else 1)
+    g = gjp.Geometry.from_cone(cg)
+    rays = parity.sampled_rays(cg, 1500, seed=n)
+    ref = oracle.rays(vol, vg, cg, *rays)
+    scale = np.abs(ref).max()
+    table = {}
+    d32 = torch.from_numpy(vol).cuda()
+    for name in ("float32", "bfloat16", "float16"):
+        dv = d32 if name == "float32" else d32.to(getattr(torch, name))
+        out = gjp.forward(dv, g, vg.h)
+        gjp.stream_status()
+        got = out[torch.from_numpy(rays[0]).cuda(), torch.from_numpy(rays[2]).cuda(),
+                  torch.from_numpy(rays[1]).cuda()].double().cpu().numpy()
+        del out
+        if name != "float32":
+            del dv
+        err = np.abs(got - ref)
+        table[name] = {"max_rel": float(err.max() / scale), "rms_rel": float(np.sqrt(np.mean(err ** 2)) / scale)}
+        assert table[name]["max_rel"] <= BOUND[name], (name, table[name])
+    # 16-bit storage keeps most of the float32 accuracy budget: bf16 rounds
+    # to 8 significant bits, fp16 to 11
+    assert table["float16"]["max_rel"] < table["bfloat16"]["max_rel"]
+    out_dir = os.environ.get("GJP_REPORT_DIR")
+    if out_dir:
+        with open(os.path.join(out_dir, f"precision_{n}.json"), "w") as f:
+            json.dump({"n": n, "views": int(len(views)), "rays": 1500, "errors": table}, f, indent=1)

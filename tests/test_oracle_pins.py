@@ -376,3 +376,18 @@ def test_golden_c1_rays_regression():
     np.testing.assert_allclose(ana, rows[:, 4], rtol=1e-12, atol=1e-12)
     # discretisation error of GJP_lin vs the analytic integrals stays small
     assert np.abs(got - ana).sum() / np.abs(ana).sum() < 0.03
+
+
+def test_linear_weights_beat_spline_weights_against_analytic_projections():
+    """Projection-quality experiment: the paper finds GJP_lin closer to the
+    analytic projections than GJP_spl (qualitative; no values printed)."""
+    for n in (64, 128):
+        vg = VolumeGeometry.centred((n, n, n), h=(64.0 / n,) * 3)
+        w = 64.0
+        g = synth.circular(3, n, n, 4 * w, 8 * w, synth.covering_pitch(w, 4 * w, 8 * w, n))
+        ell = synth.ellipsoids_world(vg)
+        vol = synth.voxelize(vg, ell, supersample=2)
+        pa = oracle.ellipsoid_project(ell, g, sub=8)
+        e_lin = np.abs(oracle.forward(vol, vg, g, wfun=0) - pa).sum() / np.abs(pa).sum()
+        e_spl = np.abs(oracle.forward(vol, vg, g, wfun=1) - pa).sum() / np.abs(pa).sum()
+        assert e_lin < e_spl, (n, e_lin, e_spl)
