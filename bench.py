@@ -51,8 +51,14 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gjp", "reference"], default="gjp")
+    p.add_argument("--workload", choices=["step", "batch"], default="step",
+                   help="step: the 512^3 hot-path step (default); batch: the 16-problem batching workload")
     p.add_argument("--n", type=int, default=512, help="volume edge (workload is defined at 512)")
     p.add_argument("--views", type=int, default=360)
+    p.add_argument("--first-views", type=int, default=0,
+                   help="keep only the first K views of the --views geometry (small profiling captures)")
+    p.add_argument("--tile-u", type=int, default=None, help="detector columns per block (library default if unset)")
+    p.add_argument("--view-group", type=int, default=None, help="views issued together (library default if unset)")
     p.add_argument("--content", choices=["random", "phantom"], default="random")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -65,6 +71,9 @@ def parse_args(argv=None):
 def workload(args):
     vg, cg = synth.scaled_c2_geometry(args.n, args.n, args.views, 10.0)
     name = f"cone-beam GJP {args.n}^3 {args.content} volume, {args.n}^2 detector, {args.views} views, 10 deg half-angle"
+    if args.first_views:
+        cg = cg.subset(range(min(args.first_views, cg.n_views)))
+        name += f" (first {cg.n_views} views)"
     return vg, cg, name
 
 
@@ -109,6 +118,47 @@ def sample_counts(vg, cg) -> np.ndarray:
             lo = np.maximum(lo, np.floor(low) + 1.0)
             hi = np.minimum(hi, np.ceil(upp) - 1.0)
         out[k] = int(np.maximum(hi - lo + 1.0, 0.0).sum())
+    return out
+
+
+def sample_counts_device(vg, cg, device):
+    """sample_counts evaluated in float64 with torch on `device` (the same
+    formula, for workloads with many large views)."""
+    import torch
+    f64 = torch.float64
+    n = torch.tensor(vg.n, dtype=f64, device=device)
+    h = torch.tensor(vg.h, dtype=f64, device=device)
+    o = torch.tensor(vg.origin, dtype=f64, device=device)
+    iv, iu = torch.meshgrid(torch.arange(cg.nv, dtype=f64, device=device),
+                            torch.arange(cg.nu, dtype=f64, device=device), indexing="ij")
+    big = 1e18
+    out = np.zeros(cg.n_views, dtype=np.int64)
+    for k in range(cg.n_views):
+        s = (torch.tensor(cg.src[k], dtype=f64, device=device) - o) / h
+        d = (torch.tensor(cg.det_origin[k], dtype=f64, device=device) + iu[..., None] *
+             torch.tensor(cg.det_u[k], dtype=f64, device=device) + iv[..., None] *
+             torch.tensor(cg.det_v[k], dtype=f64, device=device) - o) / h
+        r = d - s
+        m = torch.argmax(torch.abs(r), dim=-1)
+        rm = torch.gather(r, -1, m[..., None])[..., 0]
+        sm = s[m]
+        lo = torch.zeros_like(rm)
+        hi = n[m] - 1
+        for ax in range(3):
+            sel = m != ax
+            g = torch.where(sel, r[..., ax] / rm, torch.zeros_like(rm))
+            a = sm + (-1.0 - s[ax]) / g
+            b = sm + (n[ax] - s[ax]) / g
+            low = torch.where(g > 0, a, b)
+            upp = torch.where(g > 0, b, a)
+            inside0 = bool((s[ax] > -1.0) & (s[ax] < n[ax]))
+            low = torch.where(g == 0, torch.full_like(low, -big if inside0 else big), low)
+            upp = torch.where(g == 0, torch.full_like(upp, big if inside0 else -big), upp)
+            low = torch.where(sel, low, torch.full_like(low, -big))
+            upp = torch.where(sel, upp, torch.full_like(upp, big))
+            lo = torch.maximum(lo, torch.floor(low) + 1.0)
+            hi = torch.minimum(hi, torch.ceil(upp) - 1.0)
+        out[k] = int(torch.clamp(hi - lo + 1.0, min=0.0).sum().item())
     return out
 
 
@@ -241,7 +291,9 @@ def run_gjp(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     vg, cg, wname = workload(args)
     geom = gjp.Geometry.from_cone(cg)
-    nvox = int(np.prod(vg.n))
+    if args.tile_u is not None or args.view_group is not None:
+        tu, vgp = geom.launch
+        geom.set_launch(args.tile_u or tu, args.view_group or vgp)
 
     vol_np = make_volume(args, vg, seed=rank)
     vol32 = torch.from_numpy(vol_np).to(dev)
@@ -313,7 +365,7 @@ def run_gjp(args):
                                                  / (ms * 1e-3) / 1e9, 1)}
     dominant = max(names, key=lambda n: per_kernel_ms[n])
     kmap = {"forward_f32": "gjp_forward_kernel<float", "forward_bf16": "gjp_forward_kernel<__nv_bfloat16",
-            "adjoint_f32": "gjp_adjoint_kernel<int"}
+            "adjoint_f32": "gjp_adjoint_window_kernel<int"}
     traffic = dram_traffic(kmap[dominant])
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": kernels[dominant]["achieved_gbs"],
                 "peak": hbm, "peak_kind": peak_kind + " (copy, MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
@@ -331,6 +383,7 @@ def run_gjp(args):
         "data": "synthetic (seeded uniform [0,1) random field)" if args.content == "random"
         else "synthetic (Shepp-Logan-shaped phantom, project-owned ellipsoids)",
         "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg.n_views,
+                   "launch": {"tile_u": geom.launch[0], "view_group": geom.launch[1]},
                    "step": "forward f32 + forward bf16 + adjoint f32", "samples_per_kernel": samples_per_kernel,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
         "kernels": kernels, "roofline": roofline, "clocks": clocks,
@@ -462,10 +515,82 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_batch(args):
+    """The batching workload: 16 independent problems (synth.c5_manifest)
+    projected (a) by 16 separate gjp_forward launches, (b) by one persistent
+    batched launch with the geometries' default launch shapes, (c) the same
+    after gjp_batch_autotune, (d) (c) replayed from a CUDA graph.  One JSON
+    line; `value` is (d) in Gsamples/s."""
+    import torch
+    from paper_1609_00958_gb300 import build as libbuild
+    libbuild.build()
+    import paper_1609_00958_gb300 as gjp
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    specs = synth.c5_manifest()
+    items, samples = [], 0
+    for sp in specs:
+        vg, cg = sp.geometry()
+        vol_np = (synth.voxelize(vg, supersample=2) if sp.content == "phantom"
+                  else synth.random_field(vg.n, seed=sp.seed))
+        vol = torch.from_numpy(vol_np).to(dev).to(getattr(torch, sp.dtype))
+        g = gjp.Geometry.from_cone(cg)
+        items.append((vol, g, vg.h, None, torch.empty(g.proj_shape, device=dev)))
+        samples += int(sample_counts_device(vg, cg, dev).sum())
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def separate():
+        for vol, g, h, origin, out in items:
+            gjp.forward(vol, g, h, origin, out=out)
+
+    batch = gjp.Batch(items)
+    ms_sep = timed(separate, args.steps)
+    ms_batch = timed(batch.forward, args.steps)
+    tunings = batch.autotune(reps=2)
+    ms_tuned = timed(batch.forward, args.steps)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.forward()
+    with ClockSampler(gpu_id_for_smi(0)) as clk:
+        ms_graph = timed(graph.replay, args.steps)
+    clocks = clk.summary()
+    gsps = lambda ms: round(samples / (ms * 1e-3) / 1e9, 2)
+    print(json.dumps({
+        "metric": METRIC + " (batching form)", "value": gsps(ms_graph), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_graph, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (weights/accumulation); volume storage f32 and bf16",
+        "data": "synthetic (16 seeded problems: Shepp-Logan-shaped phantoms and uniform random fields)",
+        "config": {"workload": "batching form: 16 problems, 96^3..768^3 and 512x512x128, 90..720 views, "
+                               "128^2..768^2 detectors, 5..15 deg half-angles (synth.c5_manifest)",
+                   "samples": samples, "problems": len(items)},
+        "ms": {"separate_launches": round(ms_sep, 3), "batched": round(ms_batch, 3),
+               "batched_autotuned": round(ms_tuned, 3), "batched_autotuned_graph": round(ms_graph, 3)},
+        "gsamples_s": {"separate_launches": gsps(ms_sep), "batched": gsps(ms_batch),
+                       "batched_autotuned": gsps(ms_tuned), "batched_autotuned_graph": gsps(ms_graph)},
+        "speedup_vs_separate": round(ms_sep / ms_graph, 3),
+        "tuning": [{"tile_u": t, "view_group": v} for t, v in tunings],
+        "clocks": clocks, "gpu_launches": args.steps,
+    }), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_gjp(args)
 

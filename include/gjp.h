@@ -95,6 +95,28 @@ typedef enum { GJP_WEIGHT_LIN = 0, GJP_WEIGHT_SPL = 1 } gjp_weight;
  * GATHER).  Returns GJP_ERR_INVALID_ARG for NULL or an unknown weight. */
 gjp_status gjp_geometry_set_weight(gjp_geometry *g, gjp_weight w);
 
+/*
+ * gjp_geometry_set_launch -- launch shape of the one-thread-per-ray kernels
+ * (gather forward, prefetch forward, gather adjoint, footprint) for every
+ * later call with g.  It changes only how work is laid out on the GPU, never
+ * a result: each ray is still marched by one thread with the same
+ * arithmetic.  The paper tunes the CUDA block size per configuration; this
+ * is that knob, plus the order in which blocks are issued.
+ *   tile_u     : detector columns per block, 1, 2, 4 (default) or 8; a
+ *                block is tile_u warps of 32 detector rows.
+ *   view_group : 1 .. 64 (default 8).  Blocks are issued so that
+ *                view_group consecutive views are processed tile by tile
+ *                together (their rays cross nearly the same voxels, which
+ *                then come from the L2 cache); 1 issues the views one
+ *                after another.
+ * Returns GJP_ERR_INVALID_ARG for NULL or a value outside those sets.
+ */
+gjp_status gjp_geometry_set_launch(gjp_geometry *g, int tile_u, int view_group);
+
+/* Reads back the launch shape set by gjp_geometry_set_launch (or the
+ * library defaults).  Either output pointer may be NULL. */
+gjp_status gjp_geometry_get_launch(const gjp_geometry *g, int *tile_u, int *view_group);
+
 /* Reads back the detector shape of a geometry.  Any output pointer may be NULL. */
 gjp_status gjp_geometry_info(const gjp_geometry *g, int *n_views, int *nu, int *nv);
 
@@ -117,13 +139,16 @@ gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_
 
 /* Kernel family used by gjp_forward_ex. */
 typedef enum {
-    GJP_PATH_AUTO = 0,   /* the library's fastest family for the call (currently GATHER) */
+    GJP_PATH_AUTO = 0,   /* the library's fastest family for the call (forward: GATHER,
+                            adjoint: WINDOW) */
     GJP_PATH_GATHER = 1, /* one thread per ray, taps gathered from global memory */
     GJP_PATH_SLAB = 2,   /* detector tiles stream per-plane voxel boxes into shared memory
                             with TMA; needs a 16-byte aligned volume whose z row is a
                             multiple of 16 bytes and a magnification the box sizes cover */
-    GJP_PATH_PREFETCH = 3 /* gather, with each warp's footprint a few planes ahead
+    GJP_PATH_PREFETCH = 3, /* gather, with each warp's footprint a few planes ahead
                             prefetched into L2 by TMA; same volume alignment as SLAB */
+    GJP_PATH_WINDOW = 4   /* adjoint only: each warp combines its taps in a shared-memory
+                            window and flushes it with vector reductions (see gjp_adjoint_ex) */
 } gjp_path;
 
 /*
@@ -168,9 +193,13 @@ gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, i
  * few planes in shared memory and adds the whole box to the volume with one
  * TMA bulk tensor reduction (same volume alignment conditions as the slab
  * forward; tiles with mixed driving axes fall back to the scatter);
- * GJP_PATH_AUTO takes SLAB where it applies, else GATHER.  GJP_PATH_PREFETCH
- * is not an adjoint family (GJP_ERR_INVALID_ARG).  Results agree to float32
- * rounding; neither is bitwise deterministic.
+ * GJP_PATH_WINDOW lets each warp whose 32 rays share their transverse row
+ * (a circular orbit about z with detector rows along z) combine its taps
+ * plane by plane in a small shared-memory window and add the window to the
+ * volume with 16-byte vector reductions; other warps scatter tap by tap.
+ * GJP_PATH_AUTO takes WINDOW.  GJP_PATH_PREFETCH is not an adjoint family
+ * (GJP_ERR_INVALID_ARG).  Results agree to float32 rounding; none is
+ * bitwise deterministic.
  */
 gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx, int64_t ny,
                           int64_t nz, const double voxel_size[3], const double volume_origin[3],
@@ -222,6 +251,75 @@ gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny
 gjp_status gjp_forward_noalloc(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
                                const double voxel_size[3], const double volume_origin[3],
                                const gjp_geometry *g, float *d_proj, void *stream);
+
+/*
+ * Batched forward projection: many independent problems in one persistent
+ * launch.  The paper projects one volume at a time; a batch serves callers
+ * with many small or uneven projections (several volumes, scan geometries,
+ * storage types) whose separate launches would leave the GPU partly idle.
+ */
+
+/* One forward projection of a batch: the arguments of gjp_forward. */
+typedef struct {
+    const void *d_volume;         /* device [nx][ny][nz] elements of dtype */
+    gjp_dtype dtype;
+    int64_t nx, ny, nz;
+    double voxel_size[3];         /* > 0 */
+    double volume_origin[3];      /* world centre of voxel (0,0,0); used when has_origin != 0 */
+    int has_origin;               /* 0: the centred grid */
+    const gjp_geometry *geometry; /* its views, weight function and launch shape */
+    float *d_proj;                /* device float32 [n_views][nv][nu], fully overwritten */
+} gjp_problem;
+
+/* Opaque, library-owned batch. */
+typedef struct gjp_batch gjp_batch;
+
+/*
+ * gjp_batch_create -- validates `count` problems (1 .. 256; errors as for
+ * gjp_forward, reported for the first bad problem) and prepares one work
+ * queue over all of them: every problem is cut into items (one detector
+ * tile of one view, 128 rays) and problems with the most planes per ray
+ * are queued first.  Builds each geometry's device table on the current
+ * device (as gjp_forward would) and allocates a few hundred bytes per
+ * problem; the problems array is copied, but the volumes, projections and
+ * geometries it points to must stay valid while the batch is used.  Each
+ * problem starts with its geometry's launch shape (gjp_geometry_set_launch;
+ * a tile_u of 8 becomes 4).  Make this call before capturing a stream.
+ */
+gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **out);
+
+/* Frees the batch (NULL-safe); waits for work that may still use it. */
+void gjp_batch_destroy(gjp_batch *b);
+
+/*
+ * gjp_batch_forward -- all problems of the batch in one persistent kernel
+ * launch on `stream` (preceded by a 4-byte reset of the queue counter on the
+ * same stream; nothing is allocated or synchronised, so the call can be
+ * captured into a CUDA graph).  Each projection is bitwise equal to
+ * gjp_forward of the same problem (same per-ray arithmetic and warp
+ * layout).  Batches share nothing, but two launches of the same batch must
+ * not overlap on the GPU (they share the queue counter).  Returns
+ * GJP_ERR_INVALID_ARG if the current device is not the one the batch was
+ * created on.
+ */
+gjp_status gjp_batch_forward(const gjp_batch *b, void *stream);
+
+/*
+ * gjp_batch_autotune -- for every problem, times the batched launch of that
+ * problem alone on its first 24 views for each tile shape (tile_u = 1, 2 or
+ * 4 detector columns x 128/tile_u rows) and view interleaving (1, 4, 8, 16
+ * views), `reps` timed runs after one warm-up each, and keeps the fastest.
+ * Writes those views' projections (valid results) and synchronises
+ * `stream`; not for use during stream capture.  The choice changes speed
+ * only, never a result.
+ */
+gjp_status gjp_batch_autotune(gjp_batch *b, void *stream, int reps);
+
+/* Reads (get) or sets (set) the launch shape of problem `problem` (index
+ * into the array given to gjp_batch_create).  tile_u: 1, 2 or 4;
+ * view_group: 1 .. 64.  set uploads the new queue synchronously. */
+gjp_status gjp_batch_get_tuning(const gjp_batch *b, int problem, int *tile_u, int *view_group);
+gjp_status gjp_batch_set_tuning(gjp_batch *b, int problem, int tile_u, int view_group);
 
 /* Static, human-readable name of a status code. */
 const char *gjp_status_string(gjp_status s);

@@ -16,7 +16,8 @@ import numpy as np
 from . import _capi
 from ._capi import GjpError
 
-__all__ = ["Geometry", "forward", "adjoint", "footprint_voxels", "stream_status", "GjpError", "library_path"]
+__all__ = ["Geometry", "Batch", "forward", "adjoint", "footprint_voxels", "stream_status", "GjpError",
+           "library_path"]
 
 
 def library_path() -> str:
@@ -51,6 +52,21 @@ class Geometry:
         if st != _capi.GJP_OK:
             raise GjpError(st, "gjp_geometry_set_weight")
         self.weight = weight
+
+    def set_launch(self, tile_u: int = 4, view_group: int = 8):
+        """Launch shape of the one-thread-per-ray kernels: ``tile_u`` detector
+        columns per block (1, 2, 4 or 8) and ``view_group`` views issued tile
+        by tile together.  Changes speed only, never a result."""
+        st = _capi.gjp_geometry_set_launch(self.handle, tile_u, view_group)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_geometry_set_launch")
+
+    @property
+    def launch(self):
+        st, tu, vg = _capi.gjp_geometry_get_launch(self.handle)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_geometry_get_launch")
+        return tu, vg
 
     def close(self):
         h, self.handle = getattr(self, "handle", None), None
@@ -95,7 +111,7 @@ def _stream(t, stream):
     return int(stream.cuda_stream)
 
 
-_PATHS = {"auto": 0, "gather": 1, "slab": 2, "prefetch": 3}
+_PATHS = {"auto": 0, "gather": 1, "slab": 2, "prefetch": 3, "window": 4}
 
 
 def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None, out=None, stream=None,
@@ -176,3 +192,91 @@ def stream_status(stream=None):
     st = _capi.gjp_stream_status(int(stream.cuda_stream))
     if st != _capi.GJP_OK:
         raise GjpError(st, "gjp_stream_status")
+
+
+class Batch:
+    """Many independent forward projections in one persistent launch
+    (``gjp_batch_*``).  ``problems`` is a sequence of
+    ``(volume, geometry, voxel_size, origin, out)`` with CUDA tensors on one
+    device; the tensors and geometries are kept alive by the batch and must
+    not be reallocated while it is used (their contents may change between
+    launches).  ``forward()`` launches on the current stream and can be
+    captured into a CUDA graph."""
+
+    def __init__(self, problems):
+        torch = _torch()
+        self._keep = []
+        recs = []
+        self.device = None
+        for vol, geom, h, origin, out in problems:
+            _check_cuda(vol, "volume")
+            _check_cuda(out, "out")
+            if vol.dim() != 3:
+                raise ValueError("volume must be 3-D (nx, ny, nz)")
+            if out.dtype != torch.float32 or tuple(out.shape) != geom.proj_shape or out.device != vol.device:
+                raise ValueError("out must be float32 (n_views, nv, nu) on the volume's device")
+            if self.device is None:
+                self.device = vol.device
+            elif vol.device != self.device:
+                raise ValueError("all problems of a batch live on one device")
+            r = _capi.GjpProblem()
+            r.d_volume = vol.data_ptr()
+            r.dtype = _dtype_code(vol)
+            r.nx, r.ny, r.nz = (int(v) for v in vol.shape)
+            r.voxel_size[:] = [float(v) for v in h]
+            if origin is not None:
+                r.volume_origin[:] = [float(v) for v in origin]
+                r.has_origin = 1
+            r.geometry = geom.handle
+            r.d_proj = out.data_ptr()
+            recs.append(r)
+            self._keep.append((vol, geom, out))
+        self.handle = None
+        with torch.cuda.device(self.device):
+            st, h = _capi.gjp_batch_create(recs)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_batch_create")
+        self.handle = h
+        self.outputs = [k[2] for k in self._keep]
+
+    def forward(self, stream=None):
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            s = torch.cuda.current_stream(self.device) if stream is None else stream
+            st = _capi.gjp_batch_forward(self.handle, int(s.cuda_stream))
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_batch_forward")
+        return self.outputs
+
+    def autotune(self, reps: int = 2, stream=None):
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            s = torch.cuda.current_stream(self.device) if stream is None else stream
+            st = _capi.gjp_batch_autotune(self.handle, int(s.cuda_stream), reps)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_batch_autotune")
+        return [self.tuning(i) for i in range(len(self._keep))]
+
+    def tuning(self, i: int):
+        st, tu, vg = _capi.gjp_batch_get_tuning(self.handle, i)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_batch_get_tuning")
+        return tu, vg
+
+    def set_tuning(self, i: int, tile_u: int, view_group: int):
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            st = _capi.gjp_batch_set_tuning(self.handle, i, tile_u, view_group)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_batch_set_tuning")
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            _capi.gjp_batch_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

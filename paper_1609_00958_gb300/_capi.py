@@ -33,12 +33,14 @@ GJP_PATH_AUTO = 0
 GJP_PATH_GATHER = 1
 GJP_PATH_SLAB = 2
 GJP_PATH_PREFETCH = 3
+GJP_PATH_WINDOW = 4
 
 #: every symbol include/gjp.h declares
 EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_geometry_set_weight",
-           "gjp_forward",
+           "gjp_geometry_set_launch", "gjp_geometry_get_launch", "gjp_forward",
            "gjp_forward_ex", "gjp_forward_noalloc", "gjp_stream_status", "gjp_adjoint", "gjp_adjoint_ex",
-           "gjp_footprint", "gjp_status_string")
+           "gjp_footprint", "gjp_batch_create", "gjp_batch_destroy", "gjp_batch_forward",
+           "gjp_batch_autotune", "gjp_batch_get_tuning", "gjp_batch_set_tuning", "gjp_status_string")
 
 #: view limit of gjp_forward_noalloc (GJP_NOALLOC_MAX_VIEWS in include/gjp.h)
 GJP_NOALLOC_MAX_VIEWS = 1024
@@ -48,6 +50,14 @@ _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I = ctypes.c_int
 _D3 = ctypes.POINTER(ctypes.c_double)
+
+
+class GjpProblem(ctypes.Structure):
+    """``gjp_problem`` of include/gjp.h (one forward projection of a batch)."""
+    _fields_ = [("d_volume", ctypes.c_void_p), ("dtype", ctypes.c_int), ("nx", ctypes.c_int64),
+                ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("voxel_size", ctypes.c_double * 3),
+                ("volume_origin", ctypes.c_double * 3), ("has_origin", ctypes.c_int),
+                ("geometry", ctypes.c_void_p), ("d_proj", ctypes.c_void_p)]
 
 
 class GjpError(RuntimeError):
@@ -73,6 +83,10 @@ def load(path: str | None = None):
     lib.gjp_geometry_info.restype = _I
     lib.gjp_geometry_set_weight.argtypes = [_P, _I]
     lib.gjp_geometry_set_weight.restype = _I
+    lib.gjp_geometry_set_launch.argtypes = [_P, _I, _I]
+    lib.gjp_geometry_set_launch.restype = _I
+    lib.gjp_geometry_get_launch.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]
+    lib.gjp_geometry_get_launch.restype = _I
     lib.gjp_forward.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _P]
     lib.gjp_forward.restype = _I
     lib.gjp_forward_ex.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _I, _P]
@@ -87,6 +101,18 @@ def load(path: str | None = None):
     lib.gjp_adjoint_ex.restype = _I
     lib.gjp_footprint.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P]
     lib.gjp_footprint.restype = _I
+    lib.gjp_batch_create.argtypes = [ctypes.POINTER(GjpProblem), _I, ctypes.POINTER(_P)]
+    lib.gjp_batch_create.restype = _I
+    lib.gjp_batch_destroy.argtypes = [_P]
+    lib.gjp_batch_destroy.restype = None
+    lib.gjp_batch_forward.argtypes = [_P, _P]
+    lib.gjp_batch_forward.restype = _I
+    lib.gjp_batch_autotune.argtypes = [_P, _P, _I]
+    lib.gjp_batch_autotune.restype = _I
+    lib.gjp_batch_get_tuning.argtypes = [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
+    lib.gjp_batch_get_tuning.restype = _I
+    lib.gjp_batch_set_tuning.argtypes = [_P, _I, _I, _I]
+    lib.gjp_batch_set_tuning.restype = _I
     lib.gjp_status_string.argtypes = [_I]
     lib.gjp_status_string.restype = ctypes.c_char_p
     if path is None:
@@ -139,6 +165,16 @@ def gjp_geometry_set_weight(handle, weight: int) -> int:
     return load().gjp_geometry_set_weight(_P(handle) if handle else None, int(weight))
 
 
+def gjp_geometry_set_launch(handle, tile_u: int, view_group: int) -> int:
+    return load().gjp_geometry_set_launch(_P(handle) if handle else None, int(tile_u), int(view_group))
+
+
+def gjp_geometry_get_launch(handle):
+    a, b = _I(), _I()
+    st = load().gjp_geometry_get_launch(_P(handle) if handle else None, ctypes.byref(a), ctypes.byref(b))
+    return st, a.value, b.value
+
+
 def gjp_forward(d_volume: int, dtype: int, nx: int, ny: int, nz: int, voxel_size, volume_origin,
                 geometry, d_proj: int, stream: int) -> int:
     return load().gjp_forward(_P(d_volume), int(dtype), int(nx), int(ny), int(nz), _d3(voxel_size),
@@ -184,3 +220,34 @@ def gjp_footprint(geometry, view: int, nx: int, ny: int, nz: int, voxel_size, vo
                   d_marks: int, stream: int) -> int:
     return load().gjp_footprint(_P(geometry) if geometry else None, int(view), int(nx), int(ny), int(nz),
                                 _d3(voxel_size), _d3(volume_origin), _P(d_marks), _P(stream))
+
+
+def gjp_batch_create(problems):
+    """``problems``: sequence of GjpProblem.  Returns (status, handle)."""
+    arr = (GjpProblem * max(1, len(problems)))(*problems)
+    h = _P()
+    st = load().gjp_batch_create(arr if problems else None, len(problems), ctypes.byref(h))
+    return st, (h.value if st == GJP_OK else None)
+
+
+def gjp_batch_destroy(handle) -> None:
+    if handle:
+        load().gjp_batch_destroy(_P(handle))
+
+
+def gjp_batch_forward(handle, stream: int) -> int:
+    return load().gjp_batch_forward(_P(handle) if handle else None, _P(stream))
+
+
+def gjp_batch_autotune(handle, stream: int, reps: int) -> int:
+    return load().gjp_batch_autotune(_P(handle) if handle else None, _P(stream), int(reps))
+
+
+def gjp_batch_get_tuning(handle, problem: int):
+    a, b = _I(), _I()
+    st = load().gjp_batch_get_tuning(_P(handle) if handle else None, int(problem), ctypes.byref(a), ctypes.byref(b))
+    return st, a.value, b.value
+
+
+def gjp_batch_set_tuning(handle, problem: int, tile_u: int, view_group: int) -> int:
+    return load().gjp_batch_set_tuning(_P(handle) if handle else None, int(problem), int(tile_u), int(view_group))

@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = [os.path.join(HERE, "csrc", "gjp.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "gjp.cu"), os.path.join(HERE, "csrc", "gjp_batch.cu")]
 LIB = os.path.join(HERE, "libgjp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -34,17 +34,28 @@ def stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+    """Compiles every translation unit in parallel (one nvcc each), then
+    links the shared library; returns its path."""
     if not force and not stale():
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC",
-           "-I" + INCLUDE, "-o", tmp, *SOURCES]
+    tag = f".{os.getpid()}.tmp"   # objects: <name>.<pid>.tmp.o (nvcc dispatches on the suffix)
+    flags = [*(extra or []), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    if extra:
-        cmd[1:1] = list(extra)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+        flags.insert(0, "-Xptxas=-v")
+    objs = [os.path.splitext(src)[0] + tag + ".o" for src in SOURCES]
+    procs = [subprocess.Popen([nvcc(), *flags, "-c", src, "-o", obj]) for src, obj in zip(SOURCES, objs)]
+    codes = [p.wait() for p in procs]
+    try:
+        for src, code in zip(SOURCES, codes):
+            if code != 0:
+                raise subprocess.CalledProcessError(code, f"nvcc -c {src}")
+        tmp = LIB + tag
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.unlink(obj)
     return LIB
 
 

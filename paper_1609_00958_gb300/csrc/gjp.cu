@@ -31,75 +31,9 @@
 //  * Warps run along detector v, which maps to the contiguous z index of the
 //    volume: lanes of a warp read consecutive voxels (the memory-order rule
 //    that accompanies Algorithm 1).
-#include "gjp.h"
+#include "gjp_common.cuh"
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <cmath>
-#include <cstdint>
-#include <cstring>
-#include <deque>
-#include <mutex>
-#include <new>
-#include <vector>
-
-namespace {
-
-// ---------------------------------------------------------------------------
-// Per-view device record: FP64 host quantities (index units; pixel
-// coordinates centred on the panel, u = iu - (nu-1)/2, v = iv - (nv-1)/2)
-// split into hi + lo FP32 parts.
-struct ViewParams {
-    float rh[9], rl[9];  // R0[3], RU[3], RV[3]: ray direction d - s (Eq. 2)
-    float mh[9], ml[9];  // M0[3], MU[3], MV[3]: moment (s - c) x r about the centre c
-};
-
-struct VolParams {
-    int n[3];
-    float h[3];         // voxel size (world)
-    long long s[3];     // element strides: ny*nz, nz, 1
-};
-
-#ifndef GJP_TILE_U
-#define GJP_TILE_U 4
-#endif
-#ifndef GJP_BATCH
-#define GJP_BATCH 4
-#endif
-#ifndef GJP_MIN_BLOCKS
-#define GJP_MIN_BLOCKS 8      // 8 blocks of 128 threads: 64 registers per thread
-#endif
-#ifndef GJP_SLAB_MIN_BLOCKS
-#define GJP_SLAB_MIN_BLOCKS 3
-#endif
-constexpr int kTileV = 32;          // lanes of a warp along v (contiguous z)
-constexpr int kTileU = GJP_TILE_U;  // warps of a block along u
-constexpr int kThreads = kTileV * kTileU;
-constexpr int kBatch = GJP_BATCH;   // interior planes per batch
-
-struct gjp_cache_entry {
-    int device;
-    double key[9];
-    ViewParams *d_table;
-    int box_rows, box_cols4, box_cols8;   // slab box sizes for this grid (0 = not computed)
-};
-
-}  // namespace
-
-struct gjp_geometry {
-    int n_views, nu, nv;
-    int weight = GJP_WEIGHT_LIN;          // interpolation weight function (Eq. 13 or Eq. 14)
-    std::vector<double> src, org, du, dv;
-    std::mutex mu;
-    std::deque<gjp_cache_entry> cache;   // deque: entries keep their address
-};
-
-namespace {
+namespace gjp_detail {
 
 bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
@@ -185,347 +119,18 @@ gjp_status get_table(const gjp_geometry *gc, const int64_t n[3], const double h[
     return GJP_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Device side: double-float helpers (error-free transformations with FMA).
-
-struct f2 {
-    float hi, lo;
-};
-
-__device__ __forceinline__ f2 two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-
-__device__ __forceinline__ f2 quick_two_sum(float a, float b)  // |a| >= |b|
-{
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ f2 f2_add(f2 x, f2 y)
-{
-    f2 s = two_sum(x.hi, y.hi);
-    const f2 t = two_sum(x.lo, y.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = quick_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
-    return quick_two_sum(s.hi, s.lo);
-}
-
-__device__ __forceinline__ f2 f2_mul_f(f2 x, float f)
-{
-    const float p = __fmul_rn(x.hi, f);
-    float e = __fmaf_rn(x.hi, f, -p);
-    e = __fmaf_rn(x.lo, f, e);
-    return quick_two_sum(p, e);
-}
-
-__device__ __forceinline__ f2 f2_div(f2 x, f2 y)
-{
-    const float q1 = __fdiv_rn(x.hi, y.hi);
-    const f2 r = f2_add(x, f2_mul_f(y, -q1));
-    const float q2 = __fdiv_rn(r.hi, y.hi);
-    return quick_two_sum(q1, q2);
-}
-
-__device__ __forceinline__ f2 f2_neg(f2 x) { return {-x.hi, -x.lo}; }
-
-// X0[k] + u XU[k] + v XV[k] from a hi/lo coefficient block of 9 floats.
-__device__ __forceinline__ f2 f2_affine(const float *h, const float *l, int k, float u, float v)
-{
-    const f2 x0 = {h[k], l[k]}, xu = {h[3 + k], l[3 + k]}, xv = {h[6 + k], l[6 + k]};
-    return f2_add(f2_add(x0, f2_mul_f(xu, u)), f2_mul_f(xv, v));
-}
-
-// round(x * 2^32) as a 64-bit fixed-point number (|x| < 2^30).
-__device__ __forceinline__ long long f2_to_fixed(f2 x)
-{
-    return __float2ll_rn(x.hi * 4294967296.0f) + __float2ll_rn(x.lo * 4294967296.0f);
-}
-
-template <typename X> __device__ __forceinline__ X sel3(X x0, X x1, X x2, int k)
-{
-    return k == 0 ? x0 : (k == 1 ? x1 : x2);
-}
-
-// Eq. 10: distance to the lower grid point, from the 32 fraction bits of a
-// fixed-point position (top 23 bits placed in a float mantissa of [1, 2)).
-__device__ __forceinline__ float frac_of(unsigned long long p)
-{
-    return __uint_as_float(__funnelshift_r((unsigned)p, 0x7Fu, 9)) - 1.0f;
-}
-
-__device__ __forceinline__ int floor_of(unsigned long long p) { return (int)(p >> 32); }
-
-// Weight of the upper neighbour for distance d to the lower one: w_cl = 1 -
-// w(d), which is d for w_lin (Eq. 13) and 3d^2 - 2d^3 for w_spl (Eq. 14).
-template <bool SPL> __device__ __forceinline__ float upper_weight(float d)
-{
-    return SPL ? d * d * (3.0f - 2.0f * d) : d;
-}
-
-template <typename T> __device__ __forceinline__ float load_voxel(const T *p);
-template <> __device__ __forceinline__ float load_voxel<float>(const float *p) { return __ldg(p); }
-template <> __device__ __forceinline__ float load_voxel<__nv_bfloat16>(const __nv_bfloat16 *p)
-{
-    return __bfloat162float(__ldg(p));
-}
-template <> __device__ __forceinline__ float load_voxel<__half>(const __half *p) { return __half2float(__ldg(p)); }
-
-__device__ __forceinline__ float to_float(float x) { return x; }
-__device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
-__device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
-
-// ---------------------------------------------------------------------------
-// Per-ray setup.
-
-struct Ray {
-    int m, na, nb;            // driving axis (Eq. 3) and transverse extents
-    long long sm, sa, sb;     // element strides of m, a, b
-    long long Pa, Pb;         // transverse positions at plane ic, fixed 32.32
-    long long Ga, Gb;         // increments per plane (rt_a, rt_b of Eq. 4), fixed 32.32
-    int ic;                   // anchor plane
-    int s_lo, s_hi;           // planes with a possibly non-zero tap (support)
-    int j_lo, j_hi;           // interior planes: all four taps inside the grid
-    float step;               // |h (.) rt|: world length of one plane step
-};
-
-__device__ __forceinline__ long long pos_at(long long P, long long G, int i, int ic)
-{
-    return P + (long long)(i - ic) * G;
-}
-
-// Planes i in [0, nm - 1] with lo < P + (i - ic) G < hi (fixed point,
-// strict).  A float estimate brackets the crossings; the exact integer test
-// then trims the bracket (positions are monotone in i).
-__device__ __forceinline__ void plane_interval(long long P, long long G, int ic, long long lo, long long hi,
-                                               int nm, int &a, int &b)
-{
-    if (G == 0) {
-        const bool in = lo < P && P < hi;
-        a = 0;
-        b = in ? nm - 1 : -1;
-        return;
-    }
-    const float g = __ll2float_rn(G);
-    const float t1 = __ll2float_rn(lo - P) / g, t2 = __ll2float_rn(hi - P) / g;
-    const float lim = 3.0e7f;
-    const float tmin = fmaxf(fminf(t1, t2), -lim), tmax = fminf(fmaxf(t1, t2), lim);
-    a = max(0, ic + (int)floorf(tmin) - 2);
-    b = min(nm - 1, ic + (int)ceilf(tmax) + 2);
-    while (a <= b) {
-        const long long p = pos_at(P, G, a, ic);
-        if (lo < p && p < hi) break;
-        ++a;
-    }
-    while (b >= a) {
-        const long long p = pos_at(P, G, b, ic);
-        if (lo < p && p < hi) break;
-        --b;
-    }
-}
-
-__device__ __forceinline__ void setup_ray(const ViewParams &vp, const VolParams &V, float u, float v, Ray &R)
-{
-    const f2 r0 = f2_affine(vp.rh, vp.rl, 0, u, v);
-    const f2 r1 = f2_affine(vp.rh, vp.rl, 1, u, v);
-    const f2 r2 = f2_affine(vp.rh, vp.rl, 2, u, v);
-    int m = 0;                                           // Eq. 3, ties to the lowest index
-    if (fabsf(r1.hi) > fabsf(r0.hi)) m = 1;
-    if (fabsf(r2.hi) > fabsf(sel3(r0.hi, r1.hi, r2.hi, m))) m = 2;
-    const int a = (m == 0) ? 1 : 0;
-    const int b = (m == 2) ? 1 : 2;
-    const f2 rm = sel3(r0, r1, r2, m), ra = sel3(r0, r1, r2, a), rb = sel3(r0, r1, r2, b);
-    // moment components L_a, L_b: the centre-plane crossing is
-    // q_a = -+ L_b / r_m, q_b = -+ L_a / r_m  (minus for the cyclic order (m, k, j))
-    const f2 L0 = f2_affine(vp.mh, vp.ml, 0, u, v);
-    const f2 L1 = f2_affine(vp.mh, vp.ml, 1, u, v);
-    const f2 L2 = f2_affine(vp.mh, vp.ml, 2, u, v);
-    const f2 La = sel3(L0, L1, L2, a), Lb = sel3(L0, L1, L2, b);
-    f2 qa = f2_div(Lb, rm), qb = f2_div(La, rm);
-    if (a == (m + 1) % 3) qa = f2_neg(qa);
-    if (b == (m + 1) % 3) qb = f2_neg(qb);
-    const f2 ga = f2_div(ra, rm), gb = f2_div(rb, rm);   // Eq. 4
-
-    const int nm = sel3(V.n[0], V.n[1], V.n[2], m);
-    R.m = m;
-    R.na = sel3(V.n[0], V.n[1], V.n[2], a);
-    R.nb = sel3(V.n[0], V.n[1], V.n[2], b);
-    R.sm = sel3(V.s[0], V.s[1], V.s[2], m);
-    R.sa = sel3(V.s[0], V.s[1], V.s[2], a);
-    R.sb = sel3(V.s[0], V.s[1], V.s[2], b);
-    const float cm = 0.5f * (float)(nm - 1);
-    R.ic = (nm - 1) >> 1;                                 // floor(c_m)
-    const float delta = (float)R.ic - cm;                 // 0 or -1/2
-    const f2 Pa = f2_add(f2_add(qa, {0.5f * (float)(R.na - 1), 0.0f}), f2_mul_f(ga, delta));
-    const f2 Pb = f2_add(f2_add(qb, {0.5f * (float)(R.nb - 1), 0.0f}), f2_mul_f(gb, delta));
-    R.Pa = f2_to_fixed(Pa);
-    R.Pb = f2_to_fixed(Pb);
-    R.Ga = f2_to_fixed(ga);
-    R.Gb = f2_to_fixed(gb);
-    const float hm = sel3(V.h[0], V.h[1], V.h[2], m);
-    const float ha = sel3(V.h[0], V.h[1], V.h[2], a) * ga.hi, hb = sel3(V.h[0], V.h[1], V.h[2], b) * gb.hi;
-    R.step = sqrtf(hm * hm + ha * ha + hb * hb);
-
-    // support: -1 < p < n on both transverse axes; interior: 0 <= p < n - 1
-    const long long one = 1LL << 32;
-    int sa0, sa1, sb0, sb1, ja0, ja1, jb0, jb1;
-    plane_interval(R.Pa, R.Ga, R.ic, -one, (long long)R.na * one, nm, sa0, sa1);
-    plane_interval(R.Pb, R.Gb, R.ic, -one, (long long)R.nb * one, nm, sb0, sb1);
-    plane_interval(R.Pa, R.Ga, R.ic, -1, (long long)(R.na - 1) * one, nm, ja0, ja1);
-    plane_interval(R.Pb, R.Gb, R.ic, -1, (long long)(R.nb - 1) * one, nm, jb0, jb1);
-    R.s_lo = max(sa0, sb0);
-    R.s_hi = min(sa1, sb1);
-    R.j_lo = max(max(ja0, jb0), R.s_lo);
-    R.j_hi = min(min(ja1, jb1), R.s_hi);
-}
-
-__device__ __forceinline__ void load_view(const ViewParams *__restrict__ views, int k, ViewParams &vp)
-{
-    const float *src = reinterpret_cast<const float *>(views + k);
-    float *dst = reinterpret_cast<float *>(&vp);
-#pragma unroll
-    for (int j = 0; j < 36; ++j) dst[j] = __ldg(src + j);
-}
-
-// Boundary planes: the support planes outside the interior range, visited
-// as one index list (before the interior, then after it).
-__device__ __forceinline__ int boundary_count(const Ray &R, int &n_before)
-{
-    if (R.s_lo > R.s_hi) {
-        n_before = 0;
-        return 0;
-    }
-    if (R.j_lo > R.j_hi) {
-        n_before = R.s_hi - R.s_lo + 1;
-        return n_before;
-    }
-    n_before = R.j_lo - R.s_lo;
-    return n_before + (R.s_hi - R.j_hi);
-}
-
-__device__ __forceinline__ int boundary_plane(const Ray &R, int k, int n_before)
-{
-    return k < n_before ? R.s_lo + k : R.j_hi + 1 + (k - n_before);
-}
-
-// ---------------------------------------------------------------------------
-// Forward projection: one thread per ray; blockIdx.x = detector tile
-// (v-tiles fastest), blockIdx.y = view.
-
-template <typename T, typename Index, bool ZB, bool SPL = false>
-__device__ __forceinline__ float march_interior(const T *__restrict__ vol, const Ray &R)
-{
-    // ZB: the second transverse axis is z (stride 1), true unless m == z
-    const Index sa = (Index)R.sa, sm = (Index)R.sm;
-    const Index sb = ZB ? (Index)1 : (Index)R.sb;
-    unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, R.j_lo, R.ic);
-    unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, R.j_lo, R.ic);
-    const unsigned long long ga = (unsigned long long)R.Ga, gb = (unsigned long long)R.Gb;
-    Index plane = (Index)R.j_lo * sm;
-    // two-level sum: planes of a batch are added together, batch sums are
-    // folded into a partial sum that joins the total every 4 batches, so the
-    // total sees one addition per 16 planes (float32 error ~4x smaller than
-    // a running sum over up to ~n_m planes)
-    float acc = 0.0f, part = 0.0f;
-    int nb = 0;
-    int i = R.j_lo;
-    for (; i + kBatch - 1 <= R.j_hi; i += kBatch) {
-        float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t) {
-            da[t] = upper_weight<SPL>(frac_of(pa));
-            db[t] = upper_weight<SPL>(frac_of(pb));
-            const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-            v00[t] = load_voxel(p);
-            v01[t] = load_voxel(p + sb);
-            v10[t] = load_voxel(p + sa);
-            v11[t] = load_voxel(p + sa + sb);
-            pa += ga;
-            pb += gb;
-            plane += sm;
-        }
-        float bsum = 0.0f;
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t) {
-            // Eq. 12 with the weights of Eq. 13/14, as two nested interpolations
-            const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
-            const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
-            bsum += __fmaf_rn(da[t], e1 - e0, e0);
-        }
-        part += bsum;
-        if ((++nb & 3) == 0) {
-            acc += part;
-            part = 0.0f;
-        }
-    }
-    acc += part;
-    for (; i <= R.j_hi; ++i) {
-        const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
-        const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-        const float v00 = load_voxel(p), v01 = load_voxel(p + sb);
-        const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + sb);
-        const float e0 = __fmaf_rn(db, v01 - v00, v00);
-        const float e1 = __fmaf_rn(db, v11 - v10, v10);
-        acc += __fmaf_rn(da, e1 - e0, e0);
-        pa += ga;
-        pb += gb;
-        plane += sm;
-    }
-    return acc;
-}
-
-template <typename T, typename Index, bool SPL = false>
-__device__ __forceinline__ float march_boundary(const T *__restrict__ vol, const Ray &R)
-{
-    int n_before;
-    const int nbd = boundary_count(R, n_before);
-    const Index sa = (Index)R.sa, sb = (Index)R.sb, sm = (Index)R.sm;
-    const unsigned na = (unsigned)R.na, nb = (unsigned)R.nb;
-    float acc = 0.0f;
-    for (int k = 0; k < nbd; ++k) {
-        const int i = boundary_plane(R, k, n_before);
-        const unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, i, R.ic);
-        const unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, i, R.ic);
-        const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
-        const int ia = floor_of(pa), ib = floor_of(pb);
-        const bool a0 = (unsigned)ia < na, a1 = (unsigned)(ia + 1) < na;   // zero border
-        const bool b0 = (unsigned)ib < nb, b1 = (unsigned)(ib + 1) < nb;
-        const T *p = vol + ((Index)i * sm + (Index)ia * sa + (Index)ib * sb);
-        const float v00 = (a0 && b0) ? load_voxel(p) : 0.0f;
-        const float v01 = (a0 && b1) ? load_voxel(p + sb) : 0.0f;
-        const float v10 = (a1 && b0) ? load_voxel(p + sa) : 0.0f;
-        const float v11 = (a1 && b1) ? load_voxel(p + sa + sb) : 0.0f;
-        const float e0 = __fmaf_rn(db, v01 - v00, v00);
-        const float e1 = __fmaf_rn(db, v11 - v10, v10);
-        acc += __fmaf_rn(da, e1 - e0, e0);
-    }
-    return acc;
-}
-
 template <typename T, typename Index, bool SPL>
-__global__ void __launch_bounds__(kThreads, GJP_MIN_BLOCKS) gjp_forward_kernel(
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocksMax) gjp_forward_kernel(
     const T *__restrict__ vol, VolParams V, const ViewParams *__restrict__ views,
-    int nu, int nv, int n_tv, float *__restrict__ proj)
+    int nu, int nv, int n_tv, int n_views, int view_group, float *__restrict__ proj)
 {
-    const int tile = blockIdx.x;
-    const int view = blockIdx.y;
+    int tile, view;
+    block_tile_view(n_views, view_group, tile, view);
     const int iv = (tile % n_tv) * kTileV + threadIdx.x;
-    const int iu = (tile / n_tv) * kTileU + threadIdx.y;
+    const int iu = (tile / n_tv) * (int)blockDim.y + threadIdx.y;
+    const unsigned act = __ballot_sync(0xffffffffu, iv < nv && iu < nu);
     if (iv >= nv || iu >= nu) return;
-
-    ViewParams vp;
-    load_view(views, view, vp);
-    Ray R;
-    setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
-
-    float acc = (R.m != 2) ? march_interior<T, Index, true, SPL>(vol, R) : march_interior<T, Index, false, SPL>(vol, R);
-    acc += march_boundary<T, Index, SPL>(vol, R);
-    proj[((size_t)view * nv + iv) * nu + iu] = acc * R.step;
+    proj[((size_t)view * nv + iv) * nu + iu] = forward_ray<T, Index, SPL>(vol, V, views + view, nu, nv, iu, iv, act);
 }
 
 // ---------------------------------------------------------------------------
@@ -903,14 +508,14 @@ __device__ __forceinline__ float march_interior_pf(const T *__restrict__ vol, co
 }
 
 template <typename T, typename Index>
-__global__ void __launch_bounds__(kThreads, GJP_MIN_BLOCKS) gjp_forward_pf_kernel(
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocksMax) gjp_forward_pf_kernel(
     const T *__restrict__ vol, VolParams V, const ViewParams *__restrict__ views, int nu, int nv, int n_tv,
-    const __grid_constant__ CUtensorMap pf_map, float *__restrict__ proj)
+    int n_views, int view_group, const __grid_constant__ CUtensorMap pf_map, float *__restrict__ proj)
 {
-    const int tile = blockIdx.x;
-    const int view = blockIdx.y;
+    int tile, view;
+    block_tile_view(n_views, view_group, tile, view);
     const int iv = (tile % n_tv) * kTileV + threadIdx.x;
-    const int iu = (tile / n_tv) * kTileU + threadIdx.y;
+    const int iu = (tile / n_tv) * (int)blockDim.y + threadIdx.y;
     if (iv >= nv || iu >= nu) return;
 
     ViewParams vp;
@@ -971,14 +576,14 @@ __device__ __forceinline__ void scatter_ray(const Ray &R, float ys, float *__res
 }
 
 template <typename Index, bool SPL>
-__global__ void __launch_bounds__(kThreads) gjp_adjoint_kernel(
+__global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_kernel(
     const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views,
-    int nu, int nv, int n_tv, float *__restrict__ vol)
+    int nu, int nv, int n_tv, int n_views, int view_group, float *__restrict__ vol)
 {
-    const int tile = blockIdx.x;
-    const int view = blockIdx.y;
+    int tile, view;
+    block_tile_view(n_views, view_group, tile, view);
     const int iv = (tile % n_tv) * kTileV + threadIdx.x;
-    const int iu = (tile / n_tv) * kTileU + threadIdx.y;
+    const int iu = (tile / n_tv) * (int)blockDim.y + threadIdx.y;
     if (iv >= nv || iu >= nu) return;
     const float y = __ldg(proj + ((size_t)view * nv + iv) * nu + iu);
     if (y == 0.0f) return;   // contributes exactly nothing
@@ -988,6 +593,173 @@ __global__ void __launch_bounds__(kThreads) gjp_adjoint_kernel(
     Ray R;
     setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
     scatter_ray<Index, SPL>(R, y * R.step, vol);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint, warp window.
+//
+// The transpose scatters four taps per sample.  Where all 32 rays of a warp
+// (one detector column, 32 consecutive rows) share the driving axis m != z
+// and their transverse position and increment along the other non-z axis a
+// -- which holds bit for bit for a circular orbit about z with detector
+// rows along z, because a ray's (x, y) path does not depend on its row --
+// every sample of the warp at plane i lands in the same two rows
+// (a = ia, ia + 1), weighted 1 - da and da with one da for the whole warp,
+// and in a short increasing run of z.  The warp marches its planes in step
+// and, per plane:
+//   1. sums, per z voxel, the z-weighted values ys (1 - db) and ys db of the
+//      rays that touch it.  Lane z indices never decrease and (checked once
+//      per warp) step by 0, 1 or 2 with at most two lanes on one voxel, so
+//      three warp shuffles hand each voxel's terms to one owner lane;
+//   2. owners store the sums into a 64-voxel shared-memory window with plain
+//      stores (no two owners share a voxel);
+//   3. each lane reads one 4-voxel quad of the window and adds it, scaled by
+//      1 - da or da, to row ia or ia + 1 with one 16-byte vector reduction.
+// The same sums reach the volume with a quarter of the reduction
+// instructions and no shared-memory atomics.  Warps without that structure,
+// and planes whose z run exceeds the window, scatter tap by tap.
+
+constexpr int kWin = 64;
+
+__device__ __forceinline__ void red_add_v4(float *p, float4 v)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Adds the four taps of one sample with global atomics (zero border).
+template <typename Index>
+__device__ __forceinline__ void scatter_sample(float *__restrict__ vol, Index base, Index sa, int ia, int ib,
+                                               unsigned na, int nb, float w0, float w1, float db)
+{
+    const bool a0 = (unsigned)ia < na, a1 = (unsigned)(ia + 1) < na;
+    const bool b0 = (unsigned)ib < (unsigned)nb, b1 = (unsigned)(ib + 1) < (unsigned)nb;
+    float *p = vol + (base + (Index)ia * sa + (Index)ib);
+    if (a0 && b0) atomicAdd(p, w0 * (1.0f - db));
+    if (a0 && b1) atomicAdd(p + 1, w0 * db);
+    if (a1 && b0) atomicAdd(p + sa, w1 * (1.0f - db));
+    if (a1 && b1) atomicAdd(p + sa + 1, w1 * db);
+}
+
+template <typename Index, bool SPL>
+__global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_window_kernel(
+    const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views,
+    int nu, int nv, int n_tv, int n_views, int view_group, int vec_ok, float *__restrict__ vol)
+{
+    __shared__ __align__(16) float win_all[kMaxTileU][kWin];
+    int tile, view;
+    block_tile_view(n_views, view_group, tile, view);
+    const int lane = threadIdx.x;
+    const int v_base = (tile % n_tv) * kTileV;
+    const int iv = v_base + lane;
+    const int iu = (tile / n_tv) * (int)blockDim.y + threadIdx.y;
+    if (iu >= nu || v_base >= nv) return;            // the whole warp has no ray
+    const unsigned full = 0xffffffffu;
+    float *win = win_all[threadIdx.y];
+    win[lane] = 0.0f;
+    win[lane + 32] = 0.0f;
+    __syncwarp();
+
+    // lanes past the last detector row trace the ray of their (virtual) row
+    // with weight 0, which keeps the warp's z run increasing
+    const bool have = iv < nv;
+    const float y = have ? __ldg(proj + ((size_t)view * nv + iv) * nu + iu) : 0.0f;
+    ViewParams vp;
+    load_view(views, view, vp);
+    Ray R;
+    setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
+    const float ys = y * R.step;
+
+    const int m0 = __shfl_sync(full, R.m, 0);
+    const long long Pa0 = __shfl_sync(full, R.Pa, 0), Ga0 = __shfl_sync(full, R.Ga, 0);
+    const bool uniform = __all_sync(full, R.m == m0 && R.Pa == Pa0 && R.Ga == Ga0) && m0 != 2;
+    if (!uniform) {
+        if (ys != 0.0f) scatter_ray<Index, SPL>(R, ys, vol);
+        return;
+    }
+    const bool act = ys != 0.0f && R.s_lo <= R.s_hi;
+    const int I0 = __reduce_min_sync(full, act ? R.s_lo : 0x7fffffff);
+    const int I1 = __reduce_max_sync(full, act ? R.s_hi : -1);
+    if (I0 > I1) return;                               // nothing to add (warp-uniform)
+
+    // Run structure of the lanes' z positions p_z, checked at the first and
+    // last plane (the differences between lanes are affine in the plane
+    // index, so the checks hold in between): for neighbours 0 <= dp < 2
+    // (floor steps of 0, 1 or 2) and for lanes two apart dp >= 1 (at most
+    // two lanes per voxel).
+    const long long one = 1LL << 32;
+    bool runs_ok = true;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const long long p = pos_at(R.Pb, R.Gb, e ? I1 : I0, R.ic);
+        const long long p1 = __shfl_down_sync(full, p, 1), p2 = __shfl_down_sync(full, p, 2);
+        if (lane < 31 && !(p1 - p >= 0 && p1 - p < 2 * one)) runs_ok = false;
+        if (lane < 30 && !(p2 - p >= one)) runs_ok = false;
+    }
+    runs_ok = __all_sync(full, runs_ok);
+
+    // m in {x, y}: b is z (stride 1); a, ia and da are the same on every lane
+    const Index sa = (Index)R.sa, sm = (Index)R.sm;
+    const unsigned na = (unsigned)R.na;
+    const int nb = R.nb;
+    unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, I0, R.ic);
+    unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, I0, R.ic);
+    const unsigned long long ga = (unsigned long long)R.Ga, gb = (unsigned long long)R.Gb;
+    Index plane = (Index)I0 * sm;
+    const int row_off = lane >> 4, quad = lane & 15;   // flush: lane -> (row, 4-voxel quad)
+    for (int i = I0; i <= I1; ++i) {
+        const bool on = act && i >= R.s_lo && i <= R.s_hi;
+        const int ia = floor_of(pa), ib = floor_of(pb);
+        const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
+        const int zmin = __reduce_min_sync(full, on ? ib : 0x7fffffff);
+        const int zmax = __reduce_max_sync(full, on ? ib : (int)0x80000000);
+        const int zb = zmin & ~3;                      // 16-byte aligned window start
+        if (zmin <= zmax) {
+            if (runs_ok && zmax + 2 - zb <= kWin) {
+                const float g0 = on ? ys * (1.0f - db) : 0.0f;   // to voxel ib
+                const float g1 = on ? ys * db : 0.0f;            // to voxel ib + 1
+                const int o = ib - zb;
+                const int o_dn = __shfl_down_sync(full, o, 1), o_up = __shfl_up_sync(full, o, 1);
+                const int dn = lane < 31 ? o_dn - o : 2;         // last lane: no next voxel owner
+                const int up = lane > 0 ? o - o_up : 2;          // first lane: owns its voxel
+                const float g0n = __shfl_down_sync(full, g0, 1);
+                const float g1p = __shfl_up_sync(full, g1, 1);
+                const float s0 = g0 + (dn == 0 ? g0n : 0.0f);    // voxel o, from this run of lanes
+                const float e1 = g1 + (up == 0 ? g1p : 0.0f);    // voxel o + 1, from this run
+                const float e1p = __shfl_up_sync(full, e1, 1);
+                if (up != 0) {                                   // first lane of its run owns voxel o
+                    const float val = s0 + (up == 1 ? e1p : 0.0f);
+                    if (val != 0.0f && (unsigned)o < (unsigned)kWin) win[o] = val;
+                }
+                if (dn >= 2 && e1 != 0.0f && (unsigned)(o + 1) < (unsigned)kWin) win[o + 1] = e1;
+                __syncwarp();
+                const float4 c = reinterpret_cast<const float4 *>(win)[quad];
+                __syncwarp();
+                if (row_off == 0) reinterpret_cast<float4 *>(win)[quad] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const unsigned row = (unsigned)(ia + row_off);
+                if (row < na && (c.x != 0.0f || c.y != 0.0f || c.z != 0.0f || c.w != 0.0f)) {
+                    const float wa = row_off ? da : 1.0f - da;
+                    const float4 q = make_float4(wa * c.x, wa * c.y, wa * c.z, wa * c.w);
+                    const int z0 = zb + 4 * quad;
+                    float *dst = vol + (plane + (Index)(int)row * sa + (Index)z0);
+                    if (vec_ok && z0 >= 0 && z0 + 3 < nb) {
+                        red_add_v4(dst, q);
+                    } else {                           // zero border: drop taps outside [0, nb)
+                        const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (z0 + e >= 0 && z0 + e < nb && qv[e] != 0.0f) atomicAdd(dst + e, qv[e]);
+                    }
+                }
+                __syncwarp();
+            } else if (on) {                           // no window for this plane: tap by tap
+                scatter_sample<Index>(vol, plane, sa, ia, ib, na, nb, (1.0f - da) * ys, da * ys, db);
+            }
+        }
+        pa += ga;
+        pb += gb;
+        plane += sm;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1187,13 +959,13 @@ __global__ void __launch_bounds__(kSlabWarps * 32, 3) gjp_adjoint_slab_kernel(
 // Marks every voxel that receives a non-zero interpolation weight from a
 // ray of one view (the view's compulsory volume traffic).
 template <typename Index>
-__global__ void __launch_bounds__(kThreads) gjp_footprint_kernel(
+__global__ void __launch_bounds__(kMaxThreads) gjp_footprint_kernel(
     VolParams V, const ViewParams *__restrict__ views, int view, int nu, int nv, int n_tv,
     unsigned char *__restrict__ marks)
 {
     const int tile = blockIdx.x;
     const int iv = (tile % n_tv) * kTileV + threadIdx.x;
-    const int iu = (tile / n_tv) * kTileU + threadIdx.y;
+    const int iu = (tile / n_tv) * (int)blockDim.y + threadIdx.y;
     if (iv >= nv || iu >= nu) return;
     ViewParams vp;
     load_view(views, view, vp);
@@ -1457,11 +1229,15 @@ cudaError_t launch_gather_pf(const T *vol, gjp_dtype dt, const int64_t n[3], con
     CUtensorMap map;
     if (!encode_prefetch_map(vol, dt, n, &map)) return cudaSuccess;
     const int n_tv = (g.nv + kTileV - 1) / kTileV;
-    const int n_tu = (g.nu + kTileU - 1) / kTileU;
+    const int n_tu = (g.nu + g.tile_u - 1) / g.tile_u;
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
-    const dim3 block(kTileV, kTileU);
-    if (i32) gjp_forward_pf_kernel<T, int><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, map, proj);
-    else gjp_forward_pf_kernel<T, long long><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, map, proj);
+    const dim3 block(kTileV, g.tile_u);
+    if (i32)
+        gjp_forward_pf_kernel<T, int><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, g.n_views, g.view_group,
+                                                             map, proj);
+    else
+        gjp_forward_pf_kernel<T, long long><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, g.n_views,
+                                                                   g.view_group, map, proj);
     launched = true;
     return cudaGetLastError();
 }
@@ -1471,16 +1247,19 @@ cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *ta
                           bool i32, float *proj, cudaStream_t s)
 {
     const int n_tv = (g.nv + kTileV - 1) / kTileV;
-    const int n_tu = (g.nu + kTileU - 1) / kTileU;
+    const int n_tu = (g.nu + g.tile_u - 1) / g.tile_u;
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
-    const dim3 block(kTileV, kTileU);
+    const dim3 block(kTileV, g.tile_u);
     const bool spl = g.weight == GJP_WEIGHT_SPL;
+    const int nvw = g.n_views, vgp = g.view_group;
     if (i32) {
-        if (spl) gjp_forward_kernel<T, int, true><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, proj);
-        else gjp_forward_kernel<T, int, false><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, proj);
+        if (spl) gjp_forward_kernel<T, int, true><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
+        else gjp_forward_kernel<T, int, false><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
     } else {
-        if (spl) gjp_forward_kernel<T, long long, true><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, proj);
-        else gjp_forward_kernel<T, long long, false><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, proj);
+        if (spl)
+            gjp_forward_kernel<T, long long, true><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
+        else
+            gjp_forward_kernel<T, long long, false><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
     }
     return cudaGetLastError();
 }
@@ -1614,7 +1393,9 @@ gjp_status noalloc_table_address(int dev, ViewParams **out)
     return GJP_OK;
 }
 
-}  // namespace
+}  // namespace gjp_detail
+
+using namespace gjp_detail;
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -1695,6 +1476,23 @@ gjp_status gjp_geometry_set_weight(gjp_geometry *g, gjp_weight w)
 {
     if (!g || (w != GJP_WEIGHT_LIN && w != GJP_WEIGHT_SPL)) return GJP_ERR_INVALID_ARG;
     g->weight = w;
+    return GJP_OK;
+}
+
+gjp_status gjp_geometry_set_launch(gjp_geometry *g, int tile_u, int view_group)
+{
+    if (!g || (tile_u != 1 && tile_u != 2 && tile_u != 4 && tile_u != 8) || view_group < 1 || view_group > 64)
+        return GJP_ERR_INVALID_ARG;
+    g->tile_u = tile_u;
+    g->view_group = view_group;
+    return GJP_OK;
+}
+
+gjp_status gjp_geometry_get_launch(const gjp_geometry *g, int *tile_u, int *view_group)
+{
+    if (!g) return GJP_ERR_INVALID_ARG;
+    if (tile_u) *tile_u = g->tile_u;
+    if (view_group) *view_group = g->view_group;
     return GJP_OK;
 }
 
@@ -1823,7 +1621,8 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
                           int accumulate, gjp_path path, void *stream)
 {
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
-    if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB) return GJP_ERR_INVALID_ARG;
+    if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_WINDOW)
+        return GJP_ERR_INVALID_ARG;
     int64_t n[3];
     double h[3], o[3];
     gjp_status st = check_grid(nx, ny, nz, voxel_size, volume_origin, n, h, o);
@@ -1840,6 +1639,31 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
     }
     const bool spl = g->weight == GJP_WEIGHT_SPL;
     if (path == GJP_PATH_SLAB && spl) return GJP_ERR_UNSUPPORTED;   // the slab adjoint implements w_lin only
+    if (path == GJP_PATH_WINDOW || (path == GJP_PATH_AUTO && GJP_ADJOINT_AUTO == GJP_PATH_WINDOW)) {
+        const VolParams V = make_vol(n, h);
+        const int n_tv = (g->nv + kTileV - 1) / kTileV;
+        const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
+        const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
+        const dim3 block(kTileV, g->tile_u);
+        const int nvw = g->n_views, vgp = g->view_group;
+        const int vec = ((uintptr_t)d_volume % 16 == 0 && n[2] % 4 == 0) ? 1 : 0;
+        if (fits_int32(n)) {
+            if (spl)
+                gjp_adjoint_window_kernel<int, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw,
+                                                                            vgp, vec, d_volume);
+            else
+                gjp_adjoint_window_kernel<int, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv,
+                                                                             nvw, vgp, vec, d_volume);
+        } else {
+            if (spl)
+                gjp_adjoint_window_kernel<long long, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv,
+                                                                                  n_tv, nvw, vgp, vec, d_volume);
+            else
+                gjp_adjoint_window_kernel<long long, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv,
+                                                                                   n_tv, nvw, vgp, vec, d_volume);
+        }
+        return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+    }
     if (path != GJP_PATH_GATHER && !spl) {
         cudaError_t e = cudaSuccess;
         if (try_adjoint_slab(d_proj, n, h, o, *g, *entry, d_volume, s, e))
@@ -1848,15 +1672,22 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
     }
     const VolParams V = make_vol(n, h);
     const int n_tv = (g->nv + kTileV - 1) / kTileV;
-    const int n_tu = (g->nu + kTileU - 1) / kTileU;
+    const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
-    const dim3 block(kTileV, kTileU);
+    const dim3 block(kTileV, g->tile_u);
+    const int nvw = g->n_views, vgp = g->view_group;
     if (fits_int32(n)) {
-        if (spl) gjp_adjoint_kernel<int, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, d_volume);
-        else gjp_adjoint_kernel<int, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, d_volume);
+        if (spl)
+            gjp_adjoint_kernel<int, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw, vgp, d_volume);
+        else
+            gjp_adjoint_kernel<int, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw, vgp, d_volume);
     } else {
-        if (spl) gjp_adjoint_kernel<long long, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, d_volume);
-        else gjp_adjoint_kernel<long long, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, d_volume);
+        if (spl)
+            gjp_adjoint_kernel<long long, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw, vgp,
+                                                                       d_volume);
+        else
+            gjp_adjoint_kernel<long long, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw, vgp,
+                                                                        d_volume);
     }
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
@@ -1884,9 +1715,9 @@ gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny
     const ViewParams *table = entry->d_table;
     const VolParams V = make_vol(n, h);
     const int n_tv = (g->nv + kTileV - 1) / kTileV;
-    const int n_tu = (g->nu + kTileU - 1) / kTileU;
+    const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
     const dim3 grid((unsigned)(n_tv * n_tu));
-    const dim3 block(kTileV, kTileU);
+    const dim3 block(kTileV, g->tile_u);
     cudaStream_t s = (cudaStream_t)stream;
     if (fits_int32(n)) gjp_footprint_kernel<int><<<grid, block, 0, s>>>(V, table, view, g->nu, g->nv, n_tv, d_marks);
     else gjp_footprint_kernel<long long><<<grid, block, 0, s>>>(V, table, view, g->nu, g->nv, n_tv, d_marks);

@@ -1,0 +1,542 @@
+// gjp_common.cuh -- declarations shared by the translation units of the
+// GB300 GJP library: per-view and per-volume kernel parameters, launch
+// constants, the geometry object, host helpers (defined in gjp.cu) and the
+// per-ray device code of Algorithm 1 (setup, plane march, tap gather).
+#pragma once
+
+#include "gjp.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+namespace gjp_detail {
+
+// ---------------------------------------------------------------------------
+// Per-view device record: FP64 host quantities (index units; pixel
+// coordinates centred on the panel, u = iu - (nu-1)/2, v = iv - (nv-1)/2)
+// split into hi + lo FP32 parts.
+struct ViewParams {
+    float rh[9], rl[9];  // R0[3], RU[3], RV[3]: ray direction d - s (Eq. 2)
+    float mh[9], ml[9];  // M0[3], MU[3], MV[3]: moment (s - c) x r about the centre c
+};
+
+struct VolParams {
+    int n[3];
+    float h[3];         // voxel size (world)
+    long long s[3];     // element strides: ny*nz, nz, 1
+};
+
+#ifndef GJP_TILE_U
+#define GJP_TILE_U 4
+#endif
+#ifndef GJP_BATCH
+#define GJP_BATCH 4
+#endif
+#ifndef GJP_MIN_BLOCKS
+#define GJP_MIN_BLOCKS 8      // 8 blocks of 128 threads: 64 registers per thread
+#endif
+#ifndef GJP_SLAB_MIN_BLOCKS
+#define GJP_SLAB_MIN_BLOCKS 3
+#endif
+#ifndef GJP_ADJOINT_AUTO
+#define GJP_ADJOINT_AUTO GJP_PATH_WINDOW   // adjoint family taken by GJP_PATH_AUTO
+#endif
+#ifndef GJP_ZFUSE
+#define GJP_ZFUSE 1        // interior march: plane offset carried in the z position word
+#endif
+#ifndef GJP_VIEW_GROUP
+#define GJP_VIEW_GROUP 8   // default launch order: 8 views per detector tile
+#endif
+constexpr int kTileV = 32;          // lanes of a warp along v (contiguous z)
+constexpr int kTileU = GJP_TILE_U;  // default warps of a block along u
+constexpr int kMaxTileU = 8;        // largest block: 8 warps
+constexpr int kMaxThreads = kTileV * kMaxTileU;
+constexpr int kBatch = GJP_BATCH;   // interior planes per batch
+// register budget of the one-thread-per-ray kernels: the same per-thread
+// limit as GJP_MIN_BLOCKS resident blocks of 4 warps
+constexpr int kMinBlocksMax = (GJP_MIN_BLOCKS * 4 + kMaxTileU - 1) / kMaxTileU;
+
+struct gjp_cache_entry {
+    int device;
+    double key[9];
+    ViewParams *d_table;
+    int box_rows, box_cols4, box_cols8;   // slab box sizes for this grid (0 = not computed)
+};
+
+}  // namespace gjp_detail
+
+struct gjp_geometry {
+    int n_views, nu, nv;
+    int weight = GJP_WEIGHT_LIN;          // interpolation weight function (Eq. 13 or Eq. 14)
+    int tile_u = gjp_detail::kTileU;                  // launch shape: warps (detector columns) per block
+    int view_group = GJP_VIEW_GROUP;      // launch order: views interleaved per detector tile
+    std::vector<double> src, org, du, dv;
+    std::mutex mu;
+    std::deque<gjp_detail::gjp_cache_entry> cache;   // deque: entries keep their address
+};
+
+namespace gjp_detail {
+
+// ---------------------------------------------------------------------------
+// Host helpers (gjp.cu).
+
+// Host FP64 construction of the per-view table for one volume grid.
+void build_table(const gjp_geometry &g, const int64_t n[3], const double h[3], const double o[3],
+                 std::vector<ViewParams> &out);
+// The device table for (g, current device, grid), built on first use.
+gjp_status get_table(const gjp_geometry *g, const int64_t n[3], const double h[3], const double o[3],
+                     gjp_cache_entry **out);
+// Validates a volume grid; fills n, h and the origin (centred when origin is NULL).
+gjp_status check_grid(int64_t nx, int64_t ny, int64_t nz, const double h[3], const double *origin,
+                      int64_t n[3], double hh[3], double o[3]);
+// Rejects a geometry with a source inside the interpolated support of the grid.
+gjp_status check_sources(const gjp_geometry *g, const int64_t n[3], const double h[3], const double o[3]);
+VolParams make_vol(const int64_t n[3], const double h[3]);
+// Whether every element offset the kernels form fits a signed 32-bit integer.
+bool fits_int32(const int64_t n[3]);
+size_t elem_size(gjp_dtype t);
+
+// ---------------------------------------------------------------------------
+// Device side: double-float helpers (error-free transformations with FMA).
+
+struct f2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ f2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ f2 quick_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ f2 f2_add(f2 x, f2 y)
+{
+    f2 s = two_sum(x.hi, y.hi);
+    const f2 t = two_sum(x.lo, y.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return quick_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ f2 f2_mul_f(f2 x, float f)
+{
+    const float p = __fmul_rn(x.hi, f);
+    float e = __fmaf_rn(x.hi, f, -p);
+    e = __fmaf_rn(x.lo, f, e);
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ f2 f2_div(f2 x, f2 y)
+{
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const f2 r = f2_add(x, f2_mul_f(y, -q1));
+    const float q2 = __fdiv_rn(r.hi, y.hi);
+    return quick_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ f2 f2_neg(f2 x) { return {-x.hi, -x.lo}; }
+
+// X0[k] + u XU[k] + v XV[k] from a hi/lo coefficient block of 9 floats.
+__device__ __forceinline__ f2 f2_affine(const float *h, const float *l, int k, float u, float v)
+{
+    const f2 x0 = {h[k], l[k]}, xu = {h[3 + k], l[3 + k]}, xv = {h[6 + k], l[6 + k]};
+    return f2_add(f2_add(x0, f2_mul_f(xu, u)), f2_mul_f(xv, v));
+}
+
+// round(x * 2^32) as a 64-bit fixed-point number (|x| < 2^30).
+__device__ __forceinline__ long long f2_to_fixed(f2 x)
+{
+    return __float2ll_rn(x.hi * 4294967296.0f) + __float2ll_rn(x.lo * 4294967296.0f);
+}
+
+template <typename X> __device__ __forceinline__ X sel3(X x0, X x1, X x2, int k)
+{
+    return k == 0 ? x0 : (k == 1 ? x1 : x2);
+}
+
+// Eq. 10: distance to the lower grid point, from the 32 fraction bits of a
+// fixed-point position (top 23 bits placed in a float mantissa of [1, 2)).
+__device__ __forceinline__ float frac_of(unsigned long long p)
+{
+    return __uint_as_float(__funnelshift_r((unsigned)p, 0x7Fu, 9)) - 1.0f;
+}
+
+__device__ __forceinline__ int floor_of(unsigned long long p) { return (int)(p >> 32); }
+
+// Weight of the upper neighbour for distance d to the lower one: w_cl = 1 -
+// w(d), which is d for w_lin (Eq. 13) and 3d^2 - 2d^3 for w_spl (Eq. 14).
+template <bool SPL> __device__ __forceinline__ float upper_weight(float d)
+{
+    return SPL ? d * d * (3.0f - 2.0f * d) : d;
+}
+
+template <typename T> __device__ __forceinline__ float load_voxel(const T *p);
+template <> __device__ __forceinline__ float load_voxel<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float load_voxel<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float load_voxel<__half>(const __half *p) { return __half2float(__ldg(p)); }
+
+__device__ __forceinline__ float to_float(float x) { return x; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
+
+// ---------------------------------------------------------------------------
+// Per-ray setup.
+
+struct Ray {
+    int m, na, nb;            // driving axis (Eq. 3) and transverse extents
+    long long sm, sa, sb;     // element strides of m, a, b
+    long long Pa, Pb;         // transverse positions at plane ic, fixed 32.32
+    long long Ga, Gb;         // increments per plane (rt_a, rt_b of Eq. 4), fixed 32.32
+    int ic;                   // anchor plane
+    int s_lo, s_hi;           // planes with a possibly non-zero tap (support)
+    int j_lo, j_hi;           // interior planes: all four taps inside the grid
+    float step;               // |h (.) rt|: world length of one plane step
+};
+
+__device__ __forceinline__ long long pos_at(long long P, long long G, int i, int ic)
+{
+    return P + (long long)(i - ic) * G;
+}
+
+// Planes i in [0, nm - 1] with lo < P + (i - ic) G < hi (fixed point,
+// strict).  A float estimate brackets the crossings; the exact integer test
+// then trims the bracket (positions are monotone in i).
+__device__ __forceinline__ void plane_interval(long long P, long long G, int ic, long long lo, long long hi,
+                                               int nm, int &a, int &b)
+{
+    if (G == 0) {
+        const bool in = lo < P && P < hi;
+        a = 0;
+        b = in ? nm - 1 : -1;
+        return;
+    }
+    const float g = __ll2float_rn(G);
+    const float t1 = __ll2float_rn(lo - P) / g, t2 = __ll2float_rn(hi - P) / g;
+    const float lim = 3.0e7f;
+    const float tmin = fmaxf(fminf(t1, t2), -lim), tmax = fminf(fmaxf(t1, t2), lim);
+    a = max(0, ic + (int)floorf(tmin) - 2);
+    b = min(nm - 1, ic + (int)ceilf(tmax) + 2);
+    while (a <= b) {
+        const long long p = pos_at(P, G, a, ic);
+        if (lo < p && p < hi) break;
+        ++a;
+    }
+    while (b >= a) {
+        const long long p = pos_at(P, G, b, ic);
+        if (lo < p && p < hi) break;
+        --b;
+    }
+}
+
+__device__ __forceinline__ void setup_ray(const ViewParams &vp, const VolParams &V, float u, float v, Ray &R)
+{
+    const f2 r0 = f2_affine(vp.rh, vp.rl, 0, u, v);
+    const f2 r1 = f2_affine(vp.rh, vp.rl, 1, u, v);
+    const f2 r2 = f2_affine(vp.rh, vp.rl, 2, u, v);
+    int m = 0;                                           // Eq. 3, ties to the lowest index
+    if (fabsf(r1.hi) > fabsf(r0.hi)) m = 1;
+    if (fabsf(r2.hi) > fabsf(sel3(r0.hi, r1.hi, r2.hi, m))) m = 2;
+    const int a = (m == 0) ? 1 : 0;
+    const int b = (m == 2) ? 1 : 2;
+    const f2 rm = sel3(r0, r1, r2, m), ra = sel3(r0, r1, r2, a), rb = sel3(r0, r1, r2, b);
+    // moment components L_a, L_b: the centre-plane crossing is
+    // q_a = -+ L_b / r_m, q_b = -+ L_a / r_m  (minus for the cyclic order (m, k, j))
+    const f2 L0 = f2_affine(vp.mh, vp.ml, 0, u, v);
+    const f2 L1 = f2_affine(vp.mh, vp.ml, 1, u, v);
+    const f2 L2 = f2_affine(vp.mh, vp.ml, 2, u, v);
+    const f2 La = sel3(L0, L1, L2, a), Lb = sel3(L0, L1, L2, b);
+    f2 qa = f2_div(Lb, rm), qb = f2_div(La, rm);
+    if (a == (m + 1) % 3) qa = f2_neg(qa);
+    if (b == (m + 1) % 3) qb = f2_neg(qb);
+    const f2 ga = f2_div(ra, rm), gb = f2_div(rb, rm);   // Eq. 4
+
+    const int nm = sel3(V.n[0], V.n[1], V.n[2], m);
+    R.m = m;
+    R.na = sel3(V.n[0], V.n[1], V.n[2], a);
+    R.nb = sel3(V.n[0], V.n[1], V.n[2], b);
+    R.sm = sel3(V.s[0], V.s[1], V.s[2], m);
+    R.sa = sel3(V.s[0], V.s[1], V.s[2], a);
+    R.sb = sel3(V.s[0], V.s[1], V.s[2], b);
+    const float cm = 0.5f * (float)(nm - 1);
+    R.ic = (nm - 1) >> 1;                                 // floor(c_m)
+    const float delta = (float)R.ic - cm;                 // 0 or -1/2
+    const f2 Pa = f2_add(f2_add(qa, {0.5f * (float)(R.na - 1), 0.0f}), f2_mul_f(ga, delta));
+    const f2 Pb = f2_add(f2_add(qb, {0.5f * (float)(R.nb - 1), 0.0f}), f2_mul_f(gb, delta));
+    R.Pa = f2_to_fixed(Pa);
+    R.Pb = f2_to_fixed(Pb);
+    R.Ga = f2_to_fixed(ga);
+    R.Gb = f2_to_fixed(gb);
+    const float hm = sel3(V.h[0], V.h[1], V.h[2], m);
+    const float ha = sel3(V.h[0], V.h[1], V.h[2], a) * ga.hi, hb = sel3(V.h[0], V.h[1], V.h[2], b) * gb.hi;
+    R.step = sqrtf(hm * hm + ha * ha + hb * hb);
+
+    // support: -1 < p < n on both transverse axes; interior: 0 <= p < n - 1
+    const long long one = 1LL << 32;
+    int sa0, sa1, sb0, sb1, ja0, ja1, jb0, jb1;
+    plane_interval(R.Pa, R.Ga, R.ic, -one, (long long)R.na * one, nm, sa0, sa1);
+    plane_interval(R.Pb, R.Gb, R.ic, -one, (long long)R.nb * one, nm, sb0, sb1);
+    plane_interval(R.Pa, R.Ga, R.ic, -1, (long long)(R.na - 1) * one, nm, ja0, ja1);
+    plane_interval(R.Pb, R.Gb, R.ic, -1, (long long)(R.nb - 1) * one, nm, jb0, jb1);
+    R.s_lo = max(sa0, sb0);
+    R.s_hi = min(sa1, sb1);
+    R.j_lo = max(max(ja0, jb0), R.s_lo);
+    R.j_hi = min(min(ja1, jb1), R.s_hi);
+}
+
+__device__ __forceinline__ void load_view(const ViewParams *__restrict__ views, int k, ViewParams &vp)
+{
+    const float *src = reinterpret_cast<const float *>(views + k);
+    float *dst = reinterpret_cast<float *>(&vp);
+#pragma unroll
+    for (int j = 0; j < 36; ++j) dst[j] = __ldg(src + j);
+}
+
+// Boundary planes: the support planes outside the interior range, visited
+// as one index list (before the interior, then after it).
+__device__ __forceinline__ int boundary_count(const Ray &R, int &n_before)
+{
+    if (R.s_lo > R.s_hi) {
+        n_before = 0;
+        return 0;
+    }
+    if (R.j_lo > R.j_hi) {
+        n_before = R.s_hi - R.s_lo + 1;
+        return n_before;
+    }
+    n_before = R.j_lo - R.s_lo;
+    return n_before + (R.s_hi - R.j_hi);
+}
+
+__device__ __forceinline__ int boundary_plane(const Ray &R, int k, int n_before)
+{
+    return k < n_before ? R.s_lo + k : R.j_hi + 1 + (k - n_before);
+}
+
+// ---------------------------------------------------------------------------
+// Block order.  The grid is (detector tiles, views); blocks are numbered
+// linearly (x fastest) and dispatched roughly in that order.  With
+// view_group = G the linear number is mapped so that G consecutive blocks
+// cover the same detector tile of G consecutive views: rays of neighbouring
+// views through the same tile sweep nearly the same voxels at nearly the
+// same time, so the L2 cache serves the later views' taps.  G = 1 is plain
+// view-major order.
+__device__ __forceinline__ void block_tile_view(int n_views, int view_group, int &tile, int &view)
+{
+    const long long n_tiles = gridDim.x;
+    const long long L = (long long)blockIdx.y * n_tiles + blockIdx.x;
+    const long long per = n_tiles * view_group;
+    const int grp = (int)(L / per);
+    const int r = (int)(L - (long long)grp * per);
+    const int v0 = grp * view_group;
+    const int gl = min(view_group, n_views - v0);   // last group may hold fewer views
+    view = v0 + r % gl;
+    tile = r / gl;
+}
+
+// ---------------------------------------------------------------------------
+// Forward projection: one thread per ray; a block is blockDim.y detector
+// columns x 32 rows (v-tiles fastest within a view).
+
+// Interior planes j_lo .. j_hi of one ray: all four taps lie inside the
+// grid, so no checks.  rev marches the same planes from j_hi down to j_lo
+// (a warp picks the direction in which its lanes start on a common plane,
+// so that they read neighbouring voxels together).
+template <typename T, typename Index, bool ZB, bool SPL = false>
+__device__ __forceinline__ float march_interior(const T *__restrict__ vol, const Ray &R, bool rev = false)
+{
+    // ZB: the second transverse axis is z (stride 1), true unless m == z
+    const Index sa = (Index)R.sa;
+    const Index sb = ZB ? (Index)1 : (Index)R.sb;
+    const int i0 = rev ? R.j_hi : R.j_lo;
+    int count = R.j_hi - R.j_lo + 1;
+    unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, i0, R.ic);
+    unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, i0, R.ic);
+    const unsigned long long ga = rev ? 0ull - (unsigned long long)R.Ga : (unsigned long long)R.Ga;
+    const unsigned long long gb = rev ? 0ull - (unsigned long long)R.Gb : (unsigned long long)R.Gb;
+    const Index sm = rev ? -(Index)R.sm : (Index)R.sm;
+    Index plane = (Index)i0 * (Index)R.sm;
+    // two-level sum: planes of a batch are added together, batch sums are
+    // folded into a partial sum that joins the total every 4 batches, so the
+    // total sees one addition per 16 planes (float32 error ~4x smaller than
+    // a running sum over up to ~n_m planes)
+    float acc = 0.0f, part = 0.0f;
+    int nb = 0;
+    if constexpr (GJP_ZFUSE && ZB && std::is_same<Index, int>::value) {
+        // b = z (stride 1) and 32-bit offsets: the plane offset rides in the
+        // integer word of the z position, so one 64-bit add advances both
+        // (interior planes have 0 <= p_z < n_z - 1, and plane + floor(p_z)
+        // < 2^31), and floor(p_z) + plane comes out of the high word
+        unsigned long long pz = pb + ((unsigned long long)(unsigned)plane << 32);
+        const unsigned long long gz = gb + ((unsigned long long)(unsigned)sm << 32);
+        for (; count >= kBatch; count -= kBatch) {
+            float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                da[t] = upper_weight<SPL>(frac_of(pa));
+                db[t] = upper_weight<SPL>(frac_of(pz));
+                const T *p = vol + (floor_of(pa) * sa + floor_of(pz));
+                v00[t] = load_voxel(p);
+                v01[t] = load_voxel(p + 1);
+                v10[t] = load_voxel(p + sa);
+                v11[t] = load_voxel(p + sa + 1);
+                pa += ga;
+                pz += gz;
+            }
+            float bsum = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                // Eq. 12 with the weights of Eq. 13/14, as two nested interpolations
+                const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
+                const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
+                bsum += __fmaf_rn(da[t], e1 - e0, e0);
+            }
+            part += bsum;
+            if ((++nb & 3) == 0) {
+                acc += part;
+                part = 0.0f;
+            }
+        }
+        acc += part;
+        for (; count > 0; --count) {
+            const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pz));
+            const T *p = vol + (floor_of(pa) * sa + floor_of(pz));
+            const float v00 = load_voxel(p), v01 = load_voxel(p + 1);
+            const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + 1);
+            const float e0 = __fmaf_rn(db, v01 - v00, v00);
+            const float e1 = __fmaf_rn(db, v11 - v10, v10);
+            acc += __fmaf_rn(da, e1 - e0, e0);
+            pa += ga;
+            pz += gz;
+        }
+        return acc;
+    } else {
+        for (; count >= kBatch; count -= kBatch) {
+            float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                da[t] = upper_weight<SPL>(frac_of(pa));
+                db[t] = upper_weight<SPL>(frac_of(pb));
+                const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
+                v00[t] = load_voxel(p);
+                v01[t] = load_voxel(p + sb);
+                v10[t] = load_voxel(p + sa);
+                v11[t] = load_voxel(p + sa + sb);
+                pa += ga;
+                pb += gb;
+                plane += sm;
+            }
+            float bsum = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
+                const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
+                bsum += __fmaf_rn(da[t], e1 - e0, e0);
+            }
+            part += bsum;
+            if ((++nb & 3) == 0) {
+                acc += part;
+                part = 0.0f;
+            }
+        }
+        acc += part;
+        for (; count > 0; --count) {
+            const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
+            const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
+            const float v00 = load_voxel(p), v01 = load_voxel(p + sb);
+            const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + sb);
+            const float e0 = __fmaf_rn(db, v01 - v00, v00);
+            const float e1 = __fmaf_rn(db, v11 - v10, v10);
+            acc += __fmaf_rn(da, e1 - e0, e0);
+            pa += ga;
+            pb += gb;
+            plane += sm;
+        }
+        return acc;
+    }
+}
+
+template <typename T, typename Index, bool SPL = false>
+__device__ __forceinline__ float march_boundary(const T *__restrict__ vol, const Ray &R)
+{
+    int n_before;
+    const int nbd = boundary_count(R, n_before);
+    const Index sa = (Index)R.sa, sb = (Index)R.sb, sm = (Index)R.sm;
+    const unsigned na = (unsigned)R.na, nb = (unsigned)R.nb;
+    float acc = 0.0f;
+    for (int k = 0; k < nbd; ++k) {
+        const int i = boundary_plane(R, k, n_before);
+        const unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, i, R.ic);
+        const unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, i, R.ic);
+        const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
+        const int ia = floor_of(pa), ib = floor_of(pb);
+        const bool a0 = (unsigned)ia < na, a1 = (unsigned)(ia + 1) < na;   // zero border
+        const bool b0 = (unsigned)ib < nb, b1 = (unsigned)(ib + 1) < nb;
+        const T *p = vol + ((Index)i * sm + (Index)ia * sa + (Index)ib * sb);
+        const float v00 = (a0 && b0) ? load_voxel(p) : 0.0f;
+        const float v01 = (a0 && b1) ? load_voxel(p + sb) : 0.0f;
+        const float v10 = (a1 && b0) ? load_voxel(p + sa) : 0.0f;
+        const float v11 = (a1 && b1) ? load_voxel(p + sa + sb) : 0.0f;
+        const float e0 = __fmaf_rn(db, v01 - v00, v00);
+        const float e1 = __fmaf_rn(db, v11 - v10, v10);
+        acc += __fmaf_rn(da, e1 - e0, e0);
+    }
+    return acc;
+}
+
+// GJP line integral of the ray through detector pixel (iu, iv) of the view
+// whose table entry is *view (Algorithm 1).  Called by every lane of the
+// warp set in `act` (the lanes that hold a ray; they share the warp-level
+// choice of march direction).
+template <typename T, typename Index, bool SPL>
+__device__ __forceinline__ float forward_ray(const T *__restrict__ vol, const VolParams &V,
+                                             const ViewParams *__restrict__ view, int nu, int nv, int iu, int iv,
+                                             unsigned act)
+{
+    ViewParams vp;
+    load_view(view, 0, vp);
+    Ray R;
+    setup_ray(vp, V, (float)iu - 0.5f * (float)(nu - 1), (float)iv - 0.5f * (float)(nv - 1), R);
+
+    // March direction: the lanes of a warp usually enter their interior
+    // planes together at one end and leave at different planes at the other
+    // (rays of a detector column cross the top or bottom face of the volume
+    // one after another).  Starting at the end where the lanes agree keeps
+    // them on a common plane, so their taps fall on neighbouring voxels.
+    const int lo_spread = __reduce_max_sync(act, R.j_lo) - __reduce_min_sync(act, R.j_lo);
+    const int hi_spread = __reduce_max_sync(act, R.j_hi) - __reduce_min_sync(act, R.j_hi);
+    const bool rev = hi_spread < lo_spread;
+
+    // the few boundary planes first: afterwards only the interior march's
+    // state stays live, which keeps the unrolled loop within the register budget
+    const float bsum = march_boundary<T, Index, SPL>(vol, R);
+    const float acc = (R.m != 2) ? march_interior<T, Index, true, SPL>(vol, R, rev)
+                                 : march_interior<T, Index, false, SPL>(vol, R, rev);
+    return (acc + bsum) * R.step;
+}
+
+}  // namespace gjp_detail

@@ -201,3 +201,48 @@ def random_geometry(rng: np.random.Generator, vg: VolumeGeometry, n_views: int,
         dv[k] = ev * pitch_v
         org[k] = det_c - (nu - 1) / 2.0 * du[k] - (nv - 1) / 2.0 * dv[k]
     return ConeGeometry(src, org, du, dv, nu, nv)
+
+
+# --- batching workload ---------------------------------------------------------
+
+@dataclass
+class BatchProblemSpec:
+    """One problem of the batching workload: a centred volume of ``n``
+    voxels (h = 1) stored as ``dtype``, projected on ``views`` views of a
+    circular cone beam whose ``half_angle`` (degrees) subtends the inscribed
+    cylinder of its in-plane extent, onto a ``det`` x ``det`` detector;
+    contents are the phantom or a uniform field from ``seed``."""
+    n: tuple
+    dtype: str
+    half_angle: float
+    views: int
+    det: int
+    content: str
+    seed: int
+
+    def geometry(self):
+        vg = VolumeGeometry.centred(self.n)
+        return vg, cone_angle_geometry(max(self.n[0], self.n[1]), self.det, self.views, self.half_angle)
+
+
+def c5_manifest(seed: int = 5, count: int = 16):
+    """Batching form: ``count`` independent problems drawn from
+    ``numpy.random.default_rng(seed)``: cubic volumes with edges 96 .. 768
+    voxels (the first problem is the anisotropic 512 x 512 x 128), float32
+    or bfloat16 storage, cone half-angle uniform in [5, 15] degrees,
+    90 .. 720 views, square detectors of 128 .. 768 pixels (any size, so
+    most detector tiles are ragged), phantom or random-field contents."""
+    rng = np.random.default_rng(seed)
+    edges = [96, 128, 160, 192, 256, 320, 384, 448, 512, 640, 768]
+    out = []
+    for k in range(count):
+        n = (512, 512, 128) if k == 0 else (int(rng.choice(edges)),) * 3
+        out.append(BatchProblemSpec(
+            n=n,
+            dtype=str(rng.choice(["float32", "bfloat16"])),
+            half_angle=float(rng.uniform(5.0, 15.0)),
+            views=int(rng.integers(90, 721)),
+            det=int(rng.integers(128, 769)),
+            content=str(rng.choice(["phantom", "random"])),
+            seed=1000 + k))
+    return out

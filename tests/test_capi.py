@@ -107,3 +107,35 @@ def test_python_layer_refuses_cpu_tensors(lib):
         gjp.forward(torch.zeros(4, 4, 4), g)
     with pytest.raises(GjpError):
         Geometry(np.zeros((2, 3)), np.zeros((2, 3)), np.zeros((2, 3)), np.zeros((2, 3)), 4, 4)
+
+
+def test_problem_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of gjp_problem has the C layout: every field offset
+    and the size, as the C compiler lays out include/gjp.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in _capi.GjpProblem._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"gjp.h\"\nint main(void){\n"
+                   + "".join(f'printf("%zu\\n", offsetof(gjp_problem, {f}));\n' for f in fields)
+                   + 'printf("%zu\\n", sizeof(gjp_problem));\nreturn 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [getattr(_capi.GjpProblem, f).offset for f in fields] + [ctypes.sizeof(_capi.GjpProblem)]
+    assert got == want
+
+
+def test_batch_create_rejects_bad_arguments_without_a_gpu(lib):
+    st, h = _capi.gjp_batch_create([])
+    assert st == _capi.GJP_ERR_INVALID_ARG and h is None
+    r = _capi.GjpProblem()            # NULL volume / geometry / projections
+    st, h = _capi.gjp_batch_create([r])
+    assert st == _capi.GJP_ERR_INVALID_ARG and h is None
+    assert _capi.gjp_batch_forward(None, 0) == _capi.GJP_ERR_INVALID_ARG
+    assert _capi.gjp_batch_autotune(None, 0, 1) == _capi.GJP_ERR_INVALID_ARG
+    assert _capi.gjp_batch_get_tuning(None, 0)[0] == _capi.GJP_ERR_INVALID_ARG
+    _capi.gjp_batch_destroy(None)

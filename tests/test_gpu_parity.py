@@ -139,7 +139,7 @@ def test_adjoint_matches_oracle_transpose(gjp, steep):
     assert err <= TOL32, err
 
 
-@pytest.mark.parametrize("path", ["gather", "slab"])
+@pytest.mark.parametrize("path", ["gather", "slab", "window"])
 @pytest.mark.parametrize("geom", ["circular", "diagonal"])
 def test_adjoint_families_match_oracle_on_aligned_volume(gjp, path, geom):
     """Volume rows of 32 floats (TMA-compatible) so the slab adjoint runs;
@@ -172,6 +172,98 @@ def test_adjoint_slab_equals_gather_full_size(gjp):
     b = gjp.adjoint(y, g, vg.n, path="slab")
     gjp.stream_status()
     assert ((a - b).abs().max() / a.abs().max()).item() < 1e-5
+
+
+@pytest.mark.parametrize("case", ["random", "random_steep", "coarse_detector", "unaligned_rows", "ragged"])
+@pytest.mark.parametrize("launch", [(4, 1), (8, 3), (1, 2)])
+def test_adjoint_window_matches_oracle(gjp, case, launch):
+    """The warp-window adjoint against the oracle's transpose on the cases
+    that leave its fast path: warps whose rays do not share a transverse
+    row (random and z-driven views: per-tap scatter), z runs wider than the
+    64-voxel window (a coarse detector: 32 rows cover ~4 voxels each),
+    z rows that are not a multiple of 4 floats (no vector reduction), a
+    detector whose last warp is partly empty, under several launch shapes."""
+    rng = np.random.default_rng(400 + len(case))
+    if case.startswith("random"):
+        vg = VolumeGeometry.centred((37, 29, 23), h=(0.8, 1.1, 1.3))
+        cg = synth.random_geometry(rng, vg, 5, 45, 37, steep=case.endswith("steep"))
+    elif case == "coarse_detector":
+        vg = VolumeGeometry.centred((40, 40, 160))
+        cg = synth.circular(4, 24, 40, 300.0, 600.0, 4.0, pitch_v=8.0)
+    elif case == "unaligned_rows":
+        vg = VolumeGeometry.centred((36, 30, 27))
+        cg = synth.cone_angle_geometry(36, 40, 5, 12.0)
+    else:
+        vg = VolumeGeometry.centred((33, 35, 44))
+        cg = synth.circular(3, 37, 45, 120.0, 240.0, 1.6, angles=[0.3, 1.9, 4.0])
+    y = rng.standard_normal((cg.n_views, cg.nv, cg.nu)).astype(np.float32)
+    g = gjp.Geometry.from_cone(cg)
+    g.set_launch(*launch)
+    out = gjp.adjoint(torch.from_numpy(y).cuda(), g, vg.n, voxel_size=vg.h, origin=vg.origin, path="window")
+    gjp.stream_status()
+    ref = oracle.adjoint(y.astype(np.float64), vg, cg)
+    err = np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err <= TOL32, err
+
+
+def test_adjoint_window_spline_weight(gjp):
+    rng = np.random.default_rng(73)
+    vg = VolumeGeometry.centred((40, 36, 32), h=(1.0, 0.9, 1.1))
+    cg = synth.cone_angle_geometry(40, 36, 5, 10.0)
+    y = rng.standard_normal((cg.n_views, cg.nv, cg.nu)).astype(np.float32)
+    g = gjp.Geometry.from_cone(cg, weight="spl")
+    out = gjp.adjoint(torch.from_numpy(y).cuda(), g, vg.n, vg.h, vg.origin, path="window")
+    gjp.stream_status()
+    ref = oracle.adjoint(y.astype(np.float64), vg, cg, wfun=1)
+    assert np.abs(out.cpu().numpy() - ref).max() <= TOL32 * np.abs(ref).max()
+
+
+def test_adjoint_window_equals_gather_full_size(gjp):
+    """Warp-window and tap-by-tap adjoints on the 512^3 / 360-view workload
+    agree to float32 summation-order rounding, in two launch orders."""
+    vg, cg = synth.c2_geometry()
+    g = gjp.Geometry.from_cone(cg)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(8)
+    y = torch.rand(cg.n_views, cg.nv, cg.nu, device="cuda", generator=gen)
+    a = gjp.adjoint(y, g, vg.n, path="gather")
+    for launch in ((4, 1), (8, 8)):
+        g.set_launch(*launch)
+        b = gjp.adjoint(y, g, vg.n, path="window")
+        gjp.stream_status()
+        assert ((a - b).abs().max() / a.abs().max()).item() < 1e-5
+
+
+def test_launch_shape_changes_no_result(gjp):
+    """tile_u and view_group reorder work only: gather forward results are
+    bitwise equal (each ray is one thread with the same arithmetic, and a
+    warp is always 32 rows of one column); the prefetch family sums its
+    planes in another order and agrees to float32 rounding; invalid shapes
+    are rejected."""
+    rng = np.random.default_rng(12)
+    vg = VolumeGeometry.centred((41, 38, 36))
+    cg = synth.cone_angle_geometry(41, 45, 7, 10.0)
+    vol = torch.from_numpy(rng.random(vg.n, dtype=np.float32)).cuda()
+    g = gjp.Geometry.from_cone(cg)
+    assert g.launch == (4, 8)
+    base = gjp.forward(vol, g, vg.h, path="gather").clone()
+    for launch in ((1, 1), (2, 5), (8, 7), (8, 64)):
+        g.set_launch(*launch)
+        assert g.launch == launch
+        for path in ("gather", "prefetch") if launch[0] != 1 else ("gather",):
+            try:
+                out = gjp.forward(vol, g, vg.h, path=path)
+            except gjp.GjpError:
+                assert path == "prefetch"          # needs a TMA-aligned volume
+                continue
+            gjp.stream_status()
+            if path == "gather":
+                assert torch.equal(out, base), (launch, path)
+            else:
+                assert ((out - base).abs().max() / base.abs().max()).item() < 1e-6, (launch, path)
+    for bad in ((3, 1), (16, 1), (4, 0), (4, 65)):
+        with pytest.raises(gjp.GjpError):
+            g.set_launch(*bad)
 
 
 def test_adjoint_accumulate(gjp):
