@@ -239,14 +239,15 @@ def peaks():
 
 def dram_traffic(kernel: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
-    None if absent or taken on a different kernel source."""
+    None if absent or taken on different kernel sources."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1609_00958_gb300", "csrc", "gjp.cu"), "rb").read()
-        if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
-            return None
+        for rel, sha in d["sources"].items():
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != sha:
+                    return None
         e = d["kernels"].get(kernel)
         return None if e is None else float(e["bytes_per_launch"])
     except (OSError, KeyError, ValueError, TypeError):
@@ -365,7 +366,7 @@ def run_gjp(args):
                                                  / (ms * 1e-3) / 1e9, 1)}
     dominant = max(names, key=lambda n: per_kernel_ms[n])
     kmap = {"forward_f32": "gjp_forward_kernel<float", "forward_bf16": "gjp_forward_kernel<__nv_bfloat16",
-            "adjoint_f32": "gjp_adjoint_window_kernel<int"}
+            "adjoint_f32": "gjp_adjoint_combine_kernel<int"}
     traffic = dram_traffic(kmap[dominant])
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": kernels[dominant]["achieved_gbs"],
                 "peak": hbm, "peak_kind": peak_kind + " (copy, MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"

@@ -140,15 +140,15 @@ gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_
 /* Kernel family used by gjp_forward_ex. */
 typedef enum {
     GJP_PATH_AUTO = 0,   /* the library's fastest family for the call (forward: GATHER,
-                            adjoint: WINDOW) */
+                            adjoint: COMBINE) */
     GJP_PATH_GATHER = 1, /* one thread per ray, taps gathered from global memory */
     GJP_PATH_SLAB = 2,   /* detector tiles stream per-plane voxel boxes into shared memory
                             with TMA; needs a 16-byte aligned volume whose z row is a
                             multiple of 16 bytes and a magnification the box sizes cover */
     GJP_PATH_PREFETCH = 3, /* gather, with each warp's footprint a few planes ahead
                             prefetched into L2 by TMA; same volume alignment as SLAB */
-    GJP_PATH_WINDOW = 4   /* adjoint only: each warp combines its taps in a shared-memory
-                            window and flushes it with vector reductions (see gjp_adjoint_ex) */
+    GJP_PATH_COMBINE = 4  /* adjoint only: neighbouring rays of a warp hand shared taps to
+                            one another before the atomic additions (see gjp_adjoint_ex) */
 } gjp_path;
 
 /*
@@ -193,11 +193,12 @@ gjp_status gjp_adjoint(const float *d_proj, const gjp_geometry *g, int64_t nx, i
  * few planes in shared memory and adds the whole box to the volume with one
  * TMA bulk tensor reduction (same volume alignment conditions as the slab
  * forward; tiles with mixed driving axes fall back to the scatter);
- * GJP_PATH_WINDOW lets each warp whose 32 rays share their transverse row
- * (a circular orbit about z with detector rows along z) combine its taps
- * plane by plane in a small shared-memory window and add the window to the
- * volume with 16-byte vector reductions; other warps scatter tap by tap.
- * GJP_PATH_AUTO takes WINDOW.  GJP_PATH_PREFETCH is not an adjoint family
+ * GJP_PATH_COMBINE lets each warp whose 32 rays share their transverse row
+ * (a circular orbit about z with detector rows along z) march its planes in
+ * step and hand each ray's upper z tap to the neighbouring ray that has the
+ * same voxel as its lower tap, so one atomic addition carries both (half
+ * the additions); other warps scatter tap by tap.  GJP_PATH_AUTO takes
+ * COMBINE.  GJP_PATH_PREFETCH is not an adjoint family
  * (GJP_ERR_INVALID_ARG).  Results agree to float32 rounding; none is
  * bitwise deterministic.
  */

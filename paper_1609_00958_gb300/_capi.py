@@ -33,7 +33,7 @@ GJP_PATH_AUTO = 0
 GJP_PATH_GATHER = 1
 GJP_PATH_SLAB = 2
 GJP_PATH_PREFETCH = 3
-GJP_PATH_WINDOW = 4
+GJP_PATH_COMBINE = 4
 
 #: every symbol include/gjp.h declares
 EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_geometry_set_weight",

@@ -596,57 +596,28 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint, warp window.
+// Adjoint, warp-combined scatter.
 //
 // The transpose scatters four taps per sample.  Where all 32 rays of a warp
 // (one detector column, 32 consecutive rows) share the driving axis m != z
 // and their transverse position and increment along the other non-z axis a
 // -- which holds bit for bit for a circular orbit about z with detector
 // rows along z, because a ray's (x, y) path does not depend on its row --
-// every sample of the warp at plane i lands in the same two rows
-// (a = ia, ia + 1), weighted 1 - da and da with one da for the whole warp,
-// and in a short increasing run of z.  The warp marches its planes in step
-// and, per plane:
-//   1. sums, per z voxel, the z-weighted values ys (1 - db) and ys db of the
-//      rays that touch it.  Lane z indices never decrease and (checked once
-//      per warp) step by 0, 1 or 2 with at most two lanes on one voxel, so
-//      three warp shuffles hand each voxel's terms to one owner lane;
-//   2. owners store the sums into a 64-voxel shared-memory window with plain
-//      stores (no two owners share a voxel);
-//   3. each lane reads one 4-voxel quad of the window and adds it, scaled by
-//      1 - da or da, to row ia or ia + 1 with one 16-byte vector reduction.
-// The same sums reach the volume with a quarter of the reduction
-// instructions and no shared-memory atomics.  Warps without that structure,
-// and planes whose z run exceeds the window, scatter tap by tap.
-
-constexpr int kWin = 64;
-
-__device__ __forceinline__ void red_add_v4(float *p, float4 v)
-{
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-
-// Adds the four taps of one sample with global atomics (zero border).
-template <typename Index>
-__device__ __forceinline__ void scatter_sample(float *__restrict__ vol, Index base, Index sa, int ia, int ib,
-                                               unsigned na, int nb, float w0, float w1, float db)
-{
-    const bool a0 = (unsigned)ia < na, a1 = (unsigned)(ia + 1) < na;
-    const bool b0 = (unsigned)ib < (unsigned)nb, b1 = (unsigned)(ib + 1) < (unsigned)nb;
-    float *p = vol + (base + (Index)ia * sa + (Index)ib);
-    if (a0 && b0) atomicAdd(p, w0 * (1.0f - db));
-    if (a0 && b1) atomicAdd(p + 1, w0 * db);
-    if (a1 && b0) atomicAdd(p + sa, w1 * (1.0f - db));
-    if (a1 && b1) atomicAdd(p + sa + 1, w1 * db);
-}
+// every sample of the warp at plane i lands in the same two rows a = ia and
+// ia + 1, weighted 1 - da and da with one da for the whole warp.  The warp
+// then marches its planes in step, and per plane a lane's upper z tap
+// (ib + 1, weight ys db) usually is the next lane's lower tap: one shuffle
+// hands it over, and the next lane adds both with a single reduction per
+// row.  A lane whose upper tap is not the next lane's lower tap (a gap, two
+// rays on one voxel, or the warp's last lane) adds it itself, so the result
+// does not depend on how the rays are spaced.  This halves the reductions
+// of the tap-by-tap scatter.  Warps without a common row scatter tap by tap.
 
 template <typename Index, bool SPL>
-__global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_window_kernel(
+__global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views,
-    int nu, int nv, int n_tv, int n_views, int view_group, int vec_ok, float *__restrict__ vol)
+    int nu, int nv, int n_tv, int n_views, int view_group, float *__restrict__ vol)
 {
-    __shared__ __align__(16) float win_all[kMaxTileU][kWin];
     int tile, view;
     block_tile_view(n_views, view_group, tile, view);
     const int lane = threadIdx.x;
@@ -655,13 +626,9 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_window_kernel(
     const int iu = (tile / n_tv) * (int)blockDim.y + threadIdx.y;
     if (iu >= nu || v_base >= nv) return;            // the whole warp has no ray
     const unsigned full = 0xffffffffu;
-    float *win = win_all[threadIdx.y];
-    win[lane] = 0.0f;
-    win[lane + 32] = 0.0f;
-    __syncwarp();
 
     // lanes past the last detector row trace the ray of their (virtual) row
-    // with weight 0, which keeps the warp's z run increasing
+    // with weight 0
     const bool have = iv < nv;
     const float y = have ? __ldg(proj + ((size_t)view * nv + iv) * nu + iu) : 0.0f;
     ViewParams vp;
@@ -682,79 +649,39 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_window_kernel(
     const int I1 = __reduce_max_sync(full, act ? R.s_hi : -1);
     if (I0 > I1) return;                               // nothing to add (warp-uniform)
 
-    // Run structure of the lanes' z positions p_z, checked at the first and
-    // last plane (the differences between lanes are affine in the plane
-    // index, so the checks hold in between): for neighbours 0 <= dp < 2
-    // (floor steps of 0, 1 or 2) and for lanes two apart dp >= 1 (at most
-    // two lanes per voxel).
-    const long long one = 1LL << 32;
-    bool runs_ok = true;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const long long p = pos_at(R.Pb, R.Gb, e ? I1 : I0, R.ic);
-        const long long p1 = __shfl_down_sync(full, p, 1), p2 = __shfl_down_sync(full, p, 2);
-        if (lane < 31 && !(p1 - p >= 0 && p1 - p < 2 * one)) runs_ok = false;
-        if (lane < 30 && !(p2 - p >= one)) runs_ok = false;
-    }
-    runs_ok = __all_sync(full, runs_ok);
-
-    // m in {x, y}: b is z (stride 1); a, ia and da are the same on every lane
+    // m in {x, y}: b is z (stride 1); a, ia and da are the same on every
+    // lane.  Planes outside a lane's support put its taps outside the grid,
+    // where the zero-border checks drop them.
+    const float yw = act ? ys : 0.0f;
     const Index sa = (Index)R.sa, sm = (Index)R.sm;
-    const unsigned na = (unsigned)R.na;
-    const int nb = R.nb;
+    const unsigned na = (unsigned)R.na, nb = (unsigned)R.nb;
     unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, I0, R.ic);
     unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, I0, R.ic);
     const unsigned long long ga = (unsigned long long)R.Ga, gb = (unsigned long long)R.Gb;
     Index plane = (Index)I0 * sm;
-    const int row_off = lane >> 4, quad = lane & 15;   // flush: lane -> (row, 4-voxel quad)
     for (int i = I0; i <= I1; ++i) {
-        const bool on = act && i >= R.s_lo && i <= R.s_hi;
         const int ia = floor_of(pa), ib = floor_of(pb);
         const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
-        const int zmin = __reduce_min_sync(full, on ? ib : 0x7fffffff);
-        const int zmax = __reduce_max_sync(full, on ? ib : (int)0x80000000);
-        const int zb = zmin & ~3;                      // 16-byte aligned window start
-        if (zmin <= zmax) {
-            if (runs_ok && zmax + 2 - zb <= kWin) {
-                const float g0 = on ? ys * (1.0f - db) : 0.0f;   // to voxel ib
-                const float g1 = on ? ys * db : 0.0f;            // to voxel ib + 1
-                const int o = ib - zb;
-                const int o_dn = __shfl_down_sync(full, o, 1), o_up = __shfl_up_sync(full, o, 1);
-                const int dn = lane < 31 ? o_dn - o : 2;         // last lane: no next voxel owner
-                const int up = lane > 0 ? o - o_up : 2;          // first lane: owns its voxel
-                const float g0n = __shfl_down_sync(full, g0, 1);
-                const float g1p = __shfl_up_sync(full, g1, 1);
-                const float s0 = g0 + (dn == 0 ? g0n : 0.0f);    // voxel o, from this run of lanes
-                const float e1 = g1 + (up == 0 ? g1p : 0.0f);    // voxel o + 1, from this run
-                const float e1p = __shfl_up_sync(full, e1, 1);
-                if (up != 0) {                                   // first lane of its run owns voxel o
-                    const float val = s0 + (up == 1 ? e1p : 0.0f);
-                    if (val != 0.0f && (unsigned)o < (unsigned)kWin) win[o] = val;
-                }
-                if (dn >= 2 && e1 != 0.0f && (unsigned)(o + 1) < (unsigned)kWin) win[o + 1] = e1;
-                __syncwarp();
-                const float4 c = reinterpret_cast<const float4 *>(win)[quad];
-                __syncwarp();
-                if (row_off == 0) reinterpret_cast<float4 *>(win)[quad] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const unsigned row = (unsigned)(ia + row_off);
-                if (row < na && (c.x != 0.0f || c.y != 0.0f || c.z != 0.0f || c.w != 0.0f)) {
-                    const float wa = row_off ? da : 1.0f - da;
-                    const float4 q = make_float4(wa * c.x, wa * c.y, wa * c.z, wa * c.w);
-                    const int z0 = zb + 4 * quad;
-                    float *dst = vol + (plane + (Index)(int)row * sa + (Index)z0);
-                    if (vec_ok && z0 >= 0 && z0 + 3 < nb) {
-                        red_add_v4(dst, q);
-                    } else {                           // zero border: drop taps outside [0, nb)
-                        const float qv[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (z0 + e >= 0 && z0 + e < nb && qv[e] != 0.0f) atomicAdd(dst + e, qv[e]);
-                    }
-                }
-                __syncwarp();
-            } else if (on) {                           // no window for this plane: tap by tap
-                scatter_sample<Index>(vol, plane, sa, ia, ib, na, nb, (1.0f - da) * ys, da * ys, db);
-            }
+        const float g1 = yw * db;                      // to voxel ib + 1
+        const float g0 = __fmaf_rn(-yw, db, yw);       // yw (1 - db), to voxel ib
+        // the previous lane's upper tap joins this lane's lower tap when they
+        // are the same voxel (lane 0 receives its own values: never taken)
+        const int ib_up = __shfl_up_sync(full, ib, 1);
+        const float g1_up = __shfl_up_sync(full, g1, 1);
+        const int ib_dn = __shfl_down_sync(full, ib, 1);
+        const float x0 = ib_up + 1 == ib ? g0 + g1_up : g0;
+        const float x1 = ib_dn == ib + 1 ? 0.0f : g1;    // kept when the next lane does not take it
+        const bool r0 = (unsigned)ia < na, r1 = (unsigned)(ia + 1) < na;   // zero border
+        const bool z0 = (unsigned)ib < nb, z1 = (unsigned)(ib + 1) < nb;
+        float *p = vol + (plane + (Index)ia * sa + (Index)ib);
+        const float wa0 = 1.0f - da;
+        if (z0 && x0 != 0.0f) {
+            if (r0) atomicAdd(p, wa0 * x0);
+            if (r1) atomicAdd(p + sa, da * x0);
+        }
+        if (z1 && x1 != 0.0f) {
+            if (r0) atomicAdd(p + 1, wa0 * x1);
+            if (r1) atomicAdd(p + sa + 1, da * x1);
         }
         pa += ga;
         pb += gb;
@@ -1621,7 +1548,7 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
                           int accumulate, gjp_path path, void *stream)
 {
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
-    if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_WINDOW)
+    if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_COMBINE)
         return GJP_ERR_INVALID_ARG;
     int64_t n[3];
     double h[3], o[3];
@@ -1639,28 +1566,27 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
     }
     const bool spl = g->weight == GJP_WEIGHT_SPL;
     if (path == GJP_PATH_SLAB && spl) return GJP_ERR_UNSUPPORTED;   // the slab adjoint implements w_lin only
-    if (path == GJP_PATH_WINDOW || (path == GJP_PATH_AUTO && GJP_ADJOINT_AUTO == GJP_PATH_WINDOW)) {
+    if (path == GJP_PATH_COMBINE || (path == GJP_PATH_AUTO && GJP_ADJOINT_AUTO == GJP_PATH_COMBINE)) {
         const VolParams V = make_vol(n, h);
         const int n_tv = (g->nv + kTileV - 1) / kTileV;
         const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
         const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
         const dim3 block(kTileV, g->tile_u);
         const int nvw = g->n_views, vgp = g->view_group;
-        const int vec = ((uintptr_t)d_volume % 16 == 0 && n[2] % 4 == 0) ? 1 : 0;
         if (fits_int32(n)) {
             if (spl)
-                gjp_adjoint_window_kernel<int, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw,
-                                                                            vgp, vec, d_volume);
+                gjp_adjoint_combine_kernel<int, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw,
+                                                                            vgp, d_volume);
             else
-                gjp_adjoint_window_kernel<int, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv,
-                                                                             nvw, vgp, vec, d_volume);
+                gjp_adjoint_combine_kernel<int, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv,
+                                                                             nvw, vgp, d_volume);
         } else {
             if (spl)
-                gjp_adjoint_window_kernel<long long, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv,
-                                                                                  n_tv, nvw, vgp, vec, d_volume);
+                gjp_adjoint_combine_kernel<long long, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv,
+                                                                                  n_tv, nvw, vgp, d_volume);
             else
-                gjp_adjoint_window_kernel<long long, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv,
-                                                                                   n_tv, nvw, vgp, vec, d_volume);
+                gjp_adjoint_combine_kernel<long long, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv,
+                                                                                   n_tv, nvw, vgp, d_volume);
         }
         return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
     }

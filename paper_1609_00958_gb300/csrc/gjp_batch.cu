@@ -27,7 +27,10 @@ namespace {
 
 constexpr int kBatchWarps = 4;                       // one block: 4 warps, 128 rays
 constexpr int kBatchThreads = kBatchWarps * 32;
-constexpr int kBatchChunk = 2;                       // items taken per queue fetch
+#ifndef GJP_BATCH_CHUNK
+#define GJP_BATCH_CHUNK 1
+#endif
+constexpr int kBatchChunk = GJP_BATCH_CHUNK;         // items taken per queue fetch
 constexpr int kBatchMaxProblems = 256;
 constexpr int kTuneViews = 24;                       // views timed per autotuner candidate
 
@@ -60,24 +63,27 @@ __device__ __forceinline__ void batch_item(const BatchProblem &P, int tile, int 
     P.proj[((size_t)view * P.nv + iv) * P.nu + iu] = val;
 }
 
-template <typename T, typename Index>
+// The kernel is instantiated with only the variants its problems need
+// (64-bit offsets, w_spl weights), which keeps its code small.
+template <typename T, typename Index, bool ANY_SPL>
 __device__ __forceinline__ void batch_item_w(const BatchProblem &P, int tile, int view, int warp, int lane)
 {
-    if (P.kind & 8) batch_item<T, Index, true>(P, tile, view, warp, lane);
+    if (ANY_SPL && (P.kind & 8)) batch_item<T, Index, ANY_SPL>(P, tile, view, warp, lane);
     else batch_item<T, Index, false>(P, tile, view, warp, lane);
 }
 
-template <typename T>
+template <typename T, bool ANY_I64, bool ANY_SPL>
 __device__ __forceinline__ void batch_item_i(const BatchProblem &P, int tile, int view, int warp, int lane)
 {
-    if (P.kind & 4) batch_item_w<T, int>(P, tile, view, warp, lane);
-    else batch_item_w<T, long long>(P, tile, view, warp, lane);
+    if (!ANY_I64 || (P.kind & 4)) batch_item_w<T, int, ANY_SPL>(P, tile, view, warp, lane);
+    else batch_item_w<T, long long, ANY_SPL>(P, tile, view, warp, lane);
 }
 
 // begins[p] = first queue index of problem p, begins[n_probs] = total.
+template <bool ANY_I64, bool ANY_SPL>
 __global__ void __launch_bounds__(kBatchThreads, 8) gjp_batch_forward_kernel(
     const BatchProblem *__restrict__ probs, const long long *__restrict__ begins, int n_probs,
-    unsigned long long *__restrict__ counter)
+    unsigned long long *__restrict__ counter, int chunk)
 {
     __shared__ long long s_begin[kBatchMaxProblems + 1];
     __shared__ unsigned long long s_item;
@@ -86,12 +92,12 @@ __global__ void __launch_bounds__(kBatchThreads, 8) gjp_batch_forward_kernel(
     const long long total = s_begin[n_probs];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, (unsigned long long)kBatchChunk);
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, (unsigned long long)chunk);
         __syncthreads();
         const long long first = (long long)s_item;
         __syncthreads();                                       // s_item is rewritten next round
         if (first >= total) break;
-        const long long last = first + kBatchChunk < total ? first + kBatchChunk : total;
+        const long long last = first + chunk < total ? first + chunk : total;
         for (long long it = first; it < last; ++it) {
             int lo = 0, hi = n_probs - 1;                      // last problem with begin <= it
             while (lo < hi) {
@@ -110,9 +116,9 @@ __global__ void __launch_bounds__(kBatchThreads, 8) gjp_batch_forward_kernel(
             const int gl = min(P.view_group, P.n_views - v0);
             const int view = v0 + r % gl, tile = r / gl;
             switch (P.kind & 3) {
-            case GJP_F32: batch_item_i<float>(P, tile, view, warp, lane); break;
-            case GJP_BF16: batch_item_i<__nv_bfloat16>(P, tile, view, warp, lane); break;
-            default: batch_item_i<__half>(P, tile, view, warp, lane); break;
+            case GJP_F32: batch_item_i<float, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
+            case GJP_BF16: batch_item_i<__nv_bfloat16, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
+            default: batch_item_i<__half, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
             }
         }
     }
@@ -129,6 +135,14 @@ void shape_problem(BatchProblem &P, int tile_u, int view_group, int n_views)
     P.items = (long long)n_views * P.n_tu * P.n_tr;
 }
 
+using BatchKernel = void (*)(const BatchProblem *, const long long *, int, unsigned long long *, int);
+
+BatchKernel batch_kernel(bool any_i64, bool any_spl)
+{
+    if (any_i64) return any_spl ? gjp_batch_forward_kernel<true, true> : gjp_batch_forward_kernel<true, false>;
+    return any_spl ? gjp_batch_forward_kernel<false, true> : gjp_batch_forward_kernel<false, false>;
+}
+
 }  // namespace
 }  // namespace gjp_detail
 
@@ -137,6 +151,7 @@ using namespace gjp_detail;
 struct gjp_batch {
     int device = -1;
     int grid = 0;
+    BatchKernel kernel = nullptr;
     std::vector<BatchProblem> probs;     // queue order
     std::vector<int> order;              // queue position -> caller's problem index
     std::vector<int> full_views;         // views of each problem (queue order)
@@ -163,7 +178,7 @@ gjp_status launch(const gjp_batch *b, const BatchProblem *d_probs, const long lo
                   cudaStream_t s)
 {
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return GJP_ERR_CUDA;
-    gjp_batch_forward_kernel<<<b->grid, kBatchThreads, 0, s>>>(d_probs, d_begins, n, b->d_counter);
+    b->kernel<<<b->grid, kBatchThreads, 0, s>>>(d_probs, d_begins, n, b->d_counter, kBatchChunk);
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
@@ -260,8 +275,14 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
         free_batch(b);
         return GJP_ERR_OOM;
     }
+    bool any_i64 = false, any_spl = false;
+    for (const BatchProblem &P : b->probs) {
+        any_i64 = any_i64 || !(P.kind & 4);
+        any_spl = any_spl || (P.kind & 8);
+    }
+    b->kernel = batch_kernel(any_i64, any_spl);
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gjp_batch_forward_kernel, kBatchThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kernel, kBatchThreads, 0) !=
             cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || per_sm < 1) {
         free_batch(b);

@@ -52,10 +52,7 @@ struct VolParams {
 #define GJP_SLAB_MIN_BLOCKS 3
 #endif
 #ifndef GJP_ADJOINT_AUTO
-#define GJP_ADJOINT_AUTO GJP_PATH_WINDOW   // adjoint family taken by GJP_PATH_AUTO
-#endif
-#ifndef GJP_ZFUSE
-#define GJP_ZFUSE 1        // interior march: plane offset carried in the z position word
+#define GJP_ADJOINT_AUTO GJP_PATH_COMBINE   // adjoint family taken by GJP_PATH_AUTO
 #endif
 #ifndef GJP_VIEW_GROUP
 #define GJP_VIEW_GROUP 8   // default launch order: 8 views per detector tile
@@ -386,98 +383,49 @@ __device__ __forceinline__ float march_interior(const T *__restrict__ vol, const
     // a running sum over up to ~n_m planes)
     float acc = 0.0f, part = 0.0f;
     int nb = 0;
-    if constexpr (GJP_ZFUSE && ZB && std::is_same<Index, int>::value) {
-        // b = z (stride 1) and 32-bit offsets: the plane offset rides in the
-        // integer word of the z position, so one 64-bit add advances both
-        // (interior planes have 0 <= p_z < n_z - 1, and plane + floor(p_z)
-        // < 2^31), and floor(p_z) + plane comes out of the high word
-        unsigned long long pz = pb + ((unsigned long long)(unsigned)plane << 32);
-        const unsigned long long gz = gb + ((unsigned long long)(unsigned)sm << 32);
-        for (; count >= kBatch; count -= kBatch) {
-            float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
+    for (; count >= kBatch; count -= kBatch) {
+        float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
 #pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                da[t] = upper_weight<SPL>(frac_of(pa));
-                db[t] = upper_weight<SPL>(frac_of(pz));
-                const T *p = vol + (floor_of(pa) * sa + floor_of(pz));
-                v00[t] = load_voxel(p);
-                v01[t] = load_voxel(p + 1);
-                v10[t] = load_voxel(p + sa);
-                v11[t] = load_voxel(p + sa + 1);
-                pa += ga;
-                pz += gz;
-            }
-            float bsum = 0.0f;
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                // Eq. 12 with the weights of Eq. 13/14, as two nested interpolations
-                const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
-                const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
-                bsum += __fmaf_rn(da[t], e1 - e0, e0);
-            }
-            part += bsum;
-            if ((++nb & 3) == 0) {
-                acc += part;
-                part = 0.0f;
-            }
-        }
-        acc += part;
-        for (; count > 0; --count) {
-            const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pz));
-            const T *p = vol + (floor_of(pa) * sa + floor_of(pz));
-            const float v00 = load_voxel(p), v01 = load_voxel(p + 1);
-            const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + 1);
-            const float e0 = __fmaf_rn(db, v01 - v00, v00);
-            const float e1 = __fmaf_rn(db, v11 - v10, v10);
-            acc += __fmaf_rn(da, e1 - e0, e0);
-            pa += ga;
-            pz += gz;
-        }
-        return acc;
-    } else {
-        for (; count >= kBatch; count -= kBatch) {
-            float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                da[t] = upper_weight<SPL>(frac_of(pa));
-                db[t] = upper_weight<SPL>(frac_of(pb));
-                const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-                v00[t] = load_voxel(p);
-                v01[t] = load_voxel(p + sb);
-                v10[t] = load_voxel(p + sa);
-                v11[t] = load_voxel(p + sa + sb);
-                pa += ga;
-                pb += gb;
-                plane += sm;
-            }
-            float bsum = 0.0f;
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
-                const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
-                bsum += __fmaf_rn(da[t], e1 - e0, e0);
-            }
-            part += bsum;
-            if ((++nb & 3) == 0) {
-                acc += part;
-                part = 0.0f;
-            }
-        }
-        acc += part;
-        for (; count > 0; --count) {
-            const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
+        for (int t = 0; t < kBatch; ++t) {
+            da[t] = upper_weight<SPL>(frac_of(pa));
+            db[t] = upper_weight<SPL>(frac_of(pb));
             const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-            const float v00 = load_voxel(p), v01 = load_voxel(p + sb);
-            const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + sb);
-            const float e0 = __fmaf_rn(db, v01 - v00, v00);
-            const float e1 = __fmaf_rn(db, v11 - v10, v10);
-            acc += __fmaf_rn(da, e1 - e0, e0);
+            v00[t] = load_voxel(p);
+            v01[t] = load_voxel(p + sb);
+            v10[t] = load_voxel(p + sa);
+            v11[t] = load_voxel(p + sa + sb);
             pa += ga;
             pb += gb;
             plane += sm;
         }
-        return acc;
+        float bsum = 0.0f;
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+            // Eq. 12 with the weights of Eq. 13/14, as two nested interpolations
+            const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
+            const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
+            bsum += __fmaf_rn(da[t], e1 - e0, e0);
+        }
+        part += bsum;
+        if ((++nb & 3) == 0) {
+            acc += part;
+            part = 0.0f;
+        }
     }
+    acc += part;
+    for (; count > 0; --count) {
+        const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
+        const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
+        const float v00 = load_voxel(p), v01 = load_voxel(p + sb);
+        const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + sb);
+        const float e0 = __fmaf_rn(db, v01 - v00, v00);
+        const float e1 = __fmaf_rn(db, v11 - v10, v10);
+        acc += __fmaf_rn(da, e1 - e0, e0);
+        pa += ga;
+        pb += gb;
+        plane += sm;
+    }
+    return acc;
 }
 
 template <typename T, typename Index, bool SPL = false>

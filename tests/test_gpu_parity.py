@@ -139,7 +139,7 @@ def test_adjoint_matches_oracle_transpose(gjp, steep):
     assert err <= TOL32, err
 
 
-@pytest.mark.parametrize("path", ["gather", "slab", "window"])
+@pytest.mark.parametrize("path", ["gather", "slab", "combine"])
 @pytest.mark.parametrize("geom", ["circular", "diagonal"])
 def test_adjoint_families_match_oracle_on_aligned_volume(gjp, path, geom):
     """Volume rows of 32 floats (TMA-compatible) so the slab adjoint runs;
@@ -174,15 +174,16 @@ def test_adjoint_slab_equals_gather_full_size(gjp):
     assert ((a - b).abs().max() / a.abs().max()).item() < 1e-5
 
 
-@pytest.mark.parametrize("case", ["random", "random_steep", "coarse_detector", "unaligned_rows", "ragged"])
+@pytest.mark.parametrize("case", ["random", "random_steep", "coarse_detector", "unaligned_rows", "dense_detector",
+                                  "ragged"])
 @pytest.mark.parametrize("launch", [(4, 1), (8, 3), (1, 2)])
-def test_adjoint_window_matches_oracle(gjp, case, launch):
-    """The warp-window adjoint against the oracle's transpose on the cases
-    that leave its fast path: warps whose rays do not share a transverse
-    row (random and z-driven views: per-tap scatter), z runs wider than the
-    64-voxel window (a coarse detector: 32 rows cover ~4 voxels each),
-    z rows that are not a multiple of 4 floats (no vector reduction), a
-    detector whose last warp is partly empty, under several launch shapes."""
+def test_adjoint_combine_matches_oracle(gjp, case, launch):
+    """The warp-combined adjoint against the oracle's transpose on the cases
+    that stress it: warps whose rays do not share a transverse row (random
+    and z-driven views: per-tap scatter), rays several voxels apart (a
+    coarse detector: no tap is shared), rays closer than a voxel (two rays
+    per voxel), an odd z row length, a detector whose last warp is partly
+    empty, under several launch shapes."""
     rng = np.random.default_rng(400 + len(case))
     if case.startswith("random"):
         vg = VolumeGeometry.centred((37, 29, 23), h=(0.8, 1.1, 1.3))
@@ -193,33 +194,36 @@ def test_adjoint_window_matches_oracle(gjp, case, launch):
     elif case == "unaligned_rows":
         vg = VolumeGeometry.centred((36, 30, 27))
         cg = synth.cone_angle_geometry(36, 40, 5, 12.0)
+    elif case == "dense_detector":
+        vg = VolumeGeometry.centred((30, 30, 24))
+        cg = synth.circular(4, 33, 70, 90.0, 180.0, 0.55)
     else:
         vg = VolumeGeometry.centred((33, 35, 44))
         cg = synth.circular(3, 37, 45, 120.0, 240.0, 1.6, angles=[0.3, 1.9, 4.0])
     y = rng.standard_normal((cg.n_views, cg.nv, cg.nu)).astype(np.float32)
     g = gjp.Geometry.from_cone(cg)
     g.set_launch(*launch)
-    out = gjp.adjoint(torch.from_numpy(y).cuda(), g, vg.n, voxel_size=vg.h, origin=vg.origin, path="window")
+    out = gjp.adjoint(torch.from_numpy(y).cuda(), g, vg.n, voxel_size=vg.h, origin=vg.origin, path="combine")
     gjp.stream_status()
     ref = oracle.adjoint(y.astype(np.float64), vg, cg)
     err = np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max()
     assert err <= TOL32, err
 
 
-def test_adjoint_window_spline_weight(gjp):
+def test_adjoint_combine_spline_weight(gjp):
     rng = np.random.default_rng(73)
     vg = VolumeGeometry.centred((40, 36, 32), h=(1.0, 0.9, 1.1))
     cg = synth.cone_angle_geometry(40, 36, 5, 10.0)
     y = rng.standard_normal((cg.n_views, cg.nv, cg.nu)).astype(np.float32)
     g = gjp.Geometry.from_cone(cg, weight="spl")
-    out = gjp.adjoint(torch.from_numpy(y).cuda(), g, vg.n, vg.h, vg.origin, path="window")
+    out = gjp.adjoint(torch.from_numpy(y).cuda(), g, vg.n, vg.h, vg.origin, path="combine")
     gjp.stream_status()
     ref = oracle.adjoint(y.astype(np.float64), vg, cg, wfun=1)
     assert np.abs(out.cpu().numpy() - ref).max() <= TOL32 * np.abs(ref).max()
 
 
-def test_adjoint_window_equals_gather_full_size(gjp):
-    """Warp-window and tap-by-tap adjoints on the 512^3 / 360-view workload
+def test_adjoint_combine_equals_gather_full_size(gjp):
+    """Warp-combined and tap-by-tap adjoints on the 512^3 / 360-view workload
     agree to float32 summation-order rounding, in two launch orders."""
     vg, cg = synth.c2_geometry()
     g = gjp.Geometry.from_cone(cg)
@@ -229,7 +233,7 @@ def test_adjoint_window_equals_gather_full_size(gjp):
     a = gjp.adjoint(y, g, vg.n, path="gather")
     for launch in ((4, 1), (8, 8)):
         g.set_launch(*launch)
-        b = gjp.adjoint(y, g, vg.n, path="window")
+        b = gjp.adjoint(y, g, vg.n, path="combine")
         gjp.stream_status()
         assert ((a - b).abs().max() / a.abs().max()).item() < 1e-5
 
