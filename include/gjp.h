@@ -147,15 +147,35 @@ typedef enum {
                             multiple of 16 bytes and a magnification the box sizes cover */
     GJP_PATH_PREFETCH = 3, /* gather, with each warp's footprint a few planes ahead
                             prefetched into L2 by TMA; same volume alignment as SLAB */
-    GJP_PATH_COMBINE = 4  /* adjoint only: neighbouring rays of a warp hand shared taps to
+    GJP_PATH_COMBINE = 4, /* adjoint only: neighbouring rays of a warp hand shared taps to
                             one another before the atomic additions (see gjp_adjoint_ex) */
+    GJP_PATH_TEXTURE = 5, /* forward only, float32 / float16 volumes: the four taps of a
+                            sample come from one texture gather (tld4) on a layered copy of
+                            the volume; exact float32 weights (see below) */
+    GJP_PATH_HWLIN = 6    /* forward only, float32 / float16 volumes, w_lin: GJP_hwlin, one
+                            hardware-filtered 3-D texture fetch per sample; the hardware
+                            quantises the interpolation weights to 1/256 (see below) */
 } gjp_path;
 
 /*
- * gjp_forward_ex -- gjp_forward with an explicit kernel family.  Both
- * families compute the same samples with the same arithmetic (results agree
- * to float32 rounding).  GJP_PATH_SLAB returns GJP_ERR_UNSUPPORTED when its
- * conditions are not met; GJP_PATH_AUTO never does.
+ * gjp_forward_ex -- gjp_forward with an explicit kernel family.  GATHER,
+ * SLAB, PREFETCH and TEXTURE compute the same samples with the same
+ * arithmetic (results agree to float32 rounding).  GJP_PATH_SLAB returns
+ * GJP_ERR_UNSUPPORTED when its conditions are not met; GJP_PATH_AUTO never
+ * does.
+ *
+ * The texture families (the texture-memory and hardware-interpolation
+ * variants of the paper's speed section) copy the volume on every call into
+ * texture arrays that the library allocates on first use and keeps with the
+ * geometry until gjp_geometry_destroy: two layered arrays (TEXTURE; twice
+ * the volume's size) or one 3-D array (HWLIN; once the volume's size).
+ * Texture border addressing supplies the zero border.  They return
+ * GJP_ERR_UNSUPPORTED for bfloat16 volumes (no such texture format), for a
+ * grid beyond the device's texture limits, and (HWLIN) for w_spl; calls of
+ * a texture family with the same geometry and grid must not overlap on the
+ * GPU (they share the arrays).  HWLIN's 1/256 weight steps put its error
+ * near 1e-4 .. 1e-3 of the projection maximum: above the float32 parity
+ * bound, so GJP_PATH_AUTO never takes it.
  */
 gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
                           const double voxel_size[3], const double volume_origin[3],

@@ -111,7 +111,7 @@ def _stream(t, stream):
     return int(stream.cuda_stream)
 
 
-_PATHS = {"auto": 0, "gather": 1, "slab": 2, "prefetch": 3, "combine": 4}
+_PATHS = {"auto": 0, "gather": 1, "slab": 2, "prefetch": 3, "combine": 4, "texture": 5, "hwlin": 6}
 
 
 def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None, out=None, stream=None,

@@ -34,6 +34,8 @@ GJP_PATH_GATHER = 1
 GJP_PATH_SLAB = 2
 GJP_PATH_PREFETCH = 3
 GJP_PATH_COMBINE = 4
+GJP_PATH_TEXTURE = 5
+GJP_PATH_HWLIN = 6
 
 #: every symbol include/gjp.h declares
 EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_geometry_set_weight",

@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = [os.path.join(HERE, "csrc", "gjp.cu"), os.path.join(HERE, "csrc", "gjp_batch.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("gjp.cu", "gjp_batch.cu", "gjp_texture.cu")]
 LIB = os.path.join(HERE, "libgjp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

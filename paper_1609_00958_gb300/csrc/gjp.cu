@@ -1200,6 +1200,8 @@ gjp_status forward_typed(const void *d_volume, gjp_dtype dt, const int64_t n[3],
     const bool i32 = fits_int32(n);
     const T *vol = static_cast<const T *>(d_volume);
     const ViewParams *table = entry.d_table;
+    if (path == GJP_PATH_TEXTURE || path == GJP_PATH_HWLIN)
+        return forward_texture(d_volume, dt, n, V, g, entry, proj, path, s);
     if ((path == GJP_PATH_PREFETCH || path == GJP_PATH_SLAB) && g.weight != GJP_WEIGHT_LIN)
         return GJP_ERR_UNSUPPORTED;   // those families implement w_lin only
     if (path == GJP_PATH_PREFETCH) {
@@ -1389,10 +1391,9 @@ void gjp_geometry_destroy(gjp_geometry *g)
         int cur = -1;
         const bool have_dev = cudaGetDevice(&cur) == cudaSuccess;
         for (auto &e : g->cache) {
-            if (e.d_table) {
-                cudaSetDevice(e.device);
-                cudaFree(e.d_table);
-            }
+            cudaSetDevice(e.device);
+            if (e.d_table) cudaFree(e.d_table);
+            free_texture_cache(e);
         }
         if (have_dev) cudaSetDevice(cur);
     }
@@ -1438,7 +1439,8 @@ gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int
 {
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
     if (dtype != GJP_F32 && dtype != GJP_BF16 && dtype != GJP_F16) return GJP_ERR_INVALID_ARG;
-    if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_PREFETCH)
+    if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_PREFETCH &&
+        path != GJP_PATH_TEXTURE && path != GJP_PATH_HWLIN)
         return GJP_ERR_INVALID_ARG;
     int64_t n[3];
     double h[3], o[3];

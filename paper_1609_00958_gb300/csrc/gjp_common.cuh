@@ -71,6 +71,7 @@ struct gjp_cache_entry {
     double key[9];
     ViewParams *d_table;
     int box_rows, box_cols4, box_cols8;   // slab box sizes for this grid (0 = not computed)
+    void *tex = nullptr;                  // texture arrays of the texture families (gjp_texture.cu)
 };
 
 }  // namespace gjp_detail
@@ -105,6 +106,11 @@ VolParams make_vol(const int64_t n[3], const double h[3]);
 // Whether every element offset the kernels form fits a signed 32-bit integer.
 bool fits_int32(const int64_t n[3]);
 size_t elem_size(gjp_dtype t);
+// Texture families (gjp_texture.cu): forward through the texture unit, and
+// release of an entry's texture arrays (with the entry's device current).
+gjp_status forward_texture(const void *d_volume, gjp_dtype dt, const int64_t n[3], const VolParams &V,
+                           const gjp_geometry &g, gjp_cache_entry &entry, float *proj, int path, cudaStream_t s);
+void free_texture_cache(gjp_cache_entry &e);
 
 // ---------------------------------------------------------------------------
 // Device side: double-float helpers (error-free transformations with FMA).

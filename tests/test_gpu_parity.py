@@ -531,3 +531,97 @@ def test_spline_weight_adjoint_matches_oracle(gjp):
             gjp.adjoint(torch.from_numpy(y).cuda(), g, vg.n, vg.h, vg.origin, path=path)
     with pytest.raises(gjp.GjpError):
         gjp.forward(torch.zeros(vg.n, device="cuda"), g, vg.h, vg.origin, path="slab")
+
+
+# --- texture families (texture memory and GJP_hwlin of the speed section) ----------
+
+def _tex_case(case):
+    rng = np.random.default_rng(500 + len(case))
+    if case == "c1_phantom":
+        vg, cg = synth.c1_geometry()
+        return synth.voxelize(vg, supersample=2), vg, cg
+    if case == "random_steep":                       # includes z-driven rays (global-memory march)
+        vg = VolumeGeometry.centred((37, 29, 23), h=(0.8, 1.1, 1.3))
+        return rng.random(vg.n, dtype=np.float32), vg, synth.random_geometry(rng, vg, 5, 45, 37, steep=True)
+    vg = VolumeGeometry((40, 36, 33), (1.0, 1.0, 1.0), (-17.0, -20.5, -15.0))
+    return rng.random(vg.n, dtype=np.float32), vg, synth.circular(5, 37, 45, 120.0, 240.0, 1.6,
+                                                                    angles=[0.2, 1.1, 2.5, 3.9, 5.6])
+
+
+@pytest.mark.parametrize("case", ["c1_phantom", "random_steep", "off_centre_ragged"])
+@pytest.mark.parametrize("dt", ["float32", "float16"])
+def test_texture_gather_family_matches_oracle(gjp, case, dt):
+    """GJP_PATH_TEXTURE (one tld4 per sample, exact float32 weights) against
+    the oracle on the stored values, every ray."""
+    vol, vg, cg = _tex_case(case)
+    stored = torch.from_numpy(vol).to(getattr(torch, dt)).float().numpy()
+    gpu, _ = _project(gjp, vol, vg, cg, dtype=getattr(torch, dt), path="texture")
+    ref = oracle.forward(stored, vg, cg)
+    views, ius, ivs = parity.all_rays(cg)
+    parity.check_rays(gpu[views, ivs, ius], stored, vg, cg, views, ius, ivs, np.abs(ref).max(), TOL32,
+                      ref=ref[views, ivs, ius])
+
+
+def test_texture_gather_spline_weight(gjp):
+    vol, vg, cg = _tex_case("off_centre_ragged")
+    g = gjp.Geometry.from_cone(cg, weight="spl")
+    out = gjp.forward(torch.from_numpy(vol).cuda(), g, vg.h, vg.origin, path="texture")
+    gjp.stream_status()
+    ref = oracle.forward(vol, vg, cg, wfun=1)
+    assert np.abs(out.cpu().numpy() - ref).max() <= TOL32 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("content", ["phantom", "random"])
+def test_texture_gather_full_size_sampled(gjp, content):
+    vg, cg = synth.c2_geometry()
+    vol = synth.voxelize(vg, supersample=1) if content == "phantom" else synth.random_field(vg.n, seed=3)
+    gpu, _ = _project(gjp, vol, vg, cg, path="texture")
+    rays = parity.sampled_rays(cg, 400, seed=11)
+    ref = oracle.rays(vol, vg, cg, *rays)
+    parity.check_rays(gpu[rays[0], rays[2], rays[1]], vol, vg, cg, *rays, np.abs(ref).max(), TOL32, ref=ref)
+
+
+def test_texture_arrays_follow_volume_contents(gjp):
+    """The cached texture arrays are refilled on every call: a second
+    volume of the same grid projects to its own gather result."""
+    rng = np.random.default_rng(7)
+    vg = VolumeGeometry.centred((40, 36, 33))
+    cg = synth.cone_angle_geometry(40, 37, 4, 10.0)
+    g = gjp.Geometry.from_cone(cg)
+    for _ in range(2):
+        vol = torch.from_numpy(rng.random(vg.n, dtype=np.float32)).cuda()
+        a = gjp.forward(vol, g, vg.h, path="texture")
+        b = gjp.forward(vol, g, vg.h, path="gather")
+        gjp.stream_status()
+        assert ((a - b).abs().max() / b.abs().max()).item() < 1e-6
+
+
+@pytest.mark.parametrize("case", ["c1_phantom", "off_centre_ragged"])
+def test_hwlin_error_against_oracle(gjp, case):
+    """GJP_hwlin: one hardware-filtered fetch per sample.  The filter's
+    1/256 weight steps bound each sample's interpolation error by
+    2^-9 (|dv_a| + |dv_b|) (plus float32 coordinates, far smaller), so the
+    projection error stays well below 5e-3 of the maximum on these smooth
+    and random volumes -- but, unlike every exact family, above 1e-6."""
+    vol, vg, cg = _tex_case(case)
+    gpu, _ = _project(gjp, vol, vg, cg, path="hwlin")
+    ref = oracle.forward(vol, vg, cg)
+    err = np.abs(gpu - ref).max() / np.abs(ref).max()
+    assert 1e-6 < err < 5e-3, err
+
+
+def test_texture_families_reject_what_they_cannot_do(gjp):
+    vg = VolumeGeometry.centred((16, 16, 16))
+    cg = synth.circular(2, 8, 8, 100.0, 200.0, 1.0)
+    g = gjp.Geometry.from_cone(cg)
+    for path in ("texture", "hwlin"):
+        with pytest.raises(gjp.GjpError) as e:
+            gjp.forward(torch.zeros(vg.n, device="cuda", dtype=torch.bfloat16), g, vg.h, path=path)
+        assert e.value.status == 2
+    gs = gjp.Geometry.from_cone(cg, weight="spl")
+    with pytest.raises(gjp.GjpError):
+        gjp.forward(torch.zeros(vg.n, device="cuda"), gs, vg.h, path="hwlin")
+    y = torch.zeros(g.proj_shape, device="cuda")
+    for path in ("texture", "hwlin"):
+        with pytest.raises(gjp.GjpError):
+            gjp.adjoint(y, g, vg.n, vg.h, path=path)
