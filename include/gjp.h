@@ -113,6 +113,25 @@ gjp_status gjp_geometry_set_weight(gjp_geometry *g, gjp_weight w);
  */
 gjp_status gjp_geometry_set_launch(gjp_geometry *g, int tile_u, int view_group);
 
+/*
+ * gjp_geometry_set_fov -- field-of-view cylinder of the paper's speed
+ * section, where the first sampling point and the number of samples of
+ * each ray follow its intersection with a cylindrical volume rather than
+ * with the bounding box.  With radius > 0 (world units) every later
+ * projection with g -- forward families, adjoints, batches, footprints --
+ * samples a ray only on the planes whose sample lies within `radius` of the
+ * line through the volume centre parallel to z (the rotation axis of a
+ * centred circular scan); 0 (the default) turns it off.  The adjoint skips
+ * the same samples, so it stays the transpose.  For a volume that is zero
+ * farther than radius - 2 voxels from that line the result equals the
+ * unclipped one (up to float32 rounding) with fewer samples; for other
+ * volumes it is the projection of the volume cut to the cylinder, with the
+ * plane decision made in float32 (a sample within ~1e-4 voxel of the
+ * cylinder wall may fall on either side).  Returns GJP_ERR_INVALID_ARG for
+ * NULL, a negative or a non-finite radius.
+ */
+gjp_status gjp_geometry_set_fov(gjp_geometry *g, double radius);
+
 /* Reads back the launch shape set by gjp_geometry_set_launch (or the
  * library defaults).  Either output pointer may be NULL. */
 gjp_status gjp_geometry_get_launch(const gjp_geometry *g, int *tile_u, int *view_group);

@@ -45,13 +45,13 @@ def _open(path: str):
     """Open a compiled oracle and declare its signatures."""
     lib = ctypes.CDLL(path)
     lib.gjp_oracle_forward.argtypes = [_P, _I, _I64, _I64, _I64, _P, _P, _I, _I, _I,
-                                       _P, _P, _P, _P, _I, _I, _P]
+                                       _P, _P, _P, _P, _I, ctypes.c_double, _I, _P]
     lib.gjp_oracle_rays.argtypes = [_P, _I, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P,
-                                    _I64, _P, _P, _P, _P, _I, _I, _P]
+                                    _I64, _P, _P, _P, _P, _I, ctypes.c_double, _I, _P]
     lib.gjp_oracle_ray_info.argtypes = [_I64, _I64, _I64, _P, _P, _P, _P, _P, _P,
                                         _I64, _P, _P, _P, _P, _P, _P]
     lib.gjp_oracle_adjoint.argtypes = [_P, _I64, _I64, _I64, _P, _P, _I, _I, _I,
-                                       _P, _P, _P, _P, _I, _I, ctypes.c_double, _P]
+                                       _P, _P, _P, _P, _I, ctypes.c_double, _I, ctypes.c_double, _P]
     lib.gjp_oracle_ellipsoid_project.argtypes = [_I, _P, _I, _I, _I, _P, _P, _P, _P,
                                                  _I, _I, _P]
     for f in (lib.gjp_oracle_forward, lib.gjp_oracle_rays, lib.gjp_oracle_ray_info,
@@ -86,8 +86,10 @@ def _geom_arrays(geom):
     return _f64(geom.src), _f64(geom.det_origin), _f64(geom.det_u), _f64(geom.det_v)
 
 
-def forward(vol, vg, geom, wfun: int = 0, threads: int = 0) -> np.ndarray:
-    """Projections ``(n_views, nv, nu)`` float64 of ``vol`` ``(nx, ny, nz)``."""
+def forward(vol, vg, geom, wfun: int = 0, threads: int = 0, fov: float = 0.0) -> np.ndarray:
+    """Projections ``(n_views, nv, nu)`` float64 of ``vol`` ``(nx, ny, nz)``;
+    ``fov`` > 0 restricts sampling to the cylinder of that world radius
+    around the axis through the volume centre parallel to z."""
     v, dt = _vol(vol)
     if tuple(v.shape) != tuple(vg.n):
         raise ValueError("volume shape does not match the volume geometry")
@@ -97,13 +99,14 @@ def forward(vol, vg, geom, wfun: int = 0, threads: int = 0) -> np.ndarray:
     rc = _load().gjp_oracle_forward(v.ctypes.data, dt, *vg.n, h.ctypes.data, o.ctypes.data,
                                     geom.n_views, geom.nu, geom.nv, src.ctypes.data,
                                     org.ctypes.data, du.ctypes.data, dv.ctypes.data,
-                                    int(wfun), int(threads), out.ctypes.data)
+                                    int(wfun), float(fov), int(threads), out.ctypes.data)
     if rc:
         raise ValueError("gjp_oracle_forward rejected its arguments")
     return out
 
 
-def rays(vol, vg, geom, views, ius, ivs, axis=None, wfun: int = 0, threads: int = 0) -> np.ndarray:
+def rays(vol, vg, geom, views, ius, ivs, axis=None, wfun: int = 0, threads: int = 0,
+         fov: float = 0.0) -> np.ndarray:
     """Line integrals of selected rays; ``axis`` (per ray, -1 = Eq. 3)
     forces the driving axis."""
     v, dt = _vol(vol)
@@ -118,7 +121,7 @@ def rays(vol, vg, geom, views, ius, ivs, axis=None, wfun: int = 0, threads: int 
     rc = _load().gjp_oracle_rays(v.ctypes.data, dt, *vg.n, h.ctypes.data, o.ctypes.data,
                                  src.ctypes.data, org.ctypes.data, du.ctypes.data, dv.ctypes.data,
                                  n, views.ctypes.data, ius.ctypes.data, ivs.ctypes.data,
-                                 None if ax is None else ax.ctypes.data, int(wfun), int(threads),
+                                 None if ax is None else ax.ctypes.data, int(wfun), float(fov), int(threads),
                                  out.ctypes.data)
     if rc:
         raise ValueError("gjp_oracle_rays rejected its arguments")
@@ -143,7 +146,8 @@ def ray_info(vg, geom, views, ius, ivs):
     return m, rt, margin
 
 
-def adjoint(proj, vg, geom, wfun: int = 0, threads: int = 0, max_bytes: float = 4e9) -> np.ndarray:
+def adjoint(proj, vg, geom, wfun: int = 0, threads: int = 0, max_bytes: float = 4e9,
+            fov: float = 0.0) -> np.ndarray:
     """``A^T proj`` as a float64 ``(nx, ny, nz)`` volume."""
     p = _f64(proj)
     if p.shape != (geom.n_views, geom.nv, geom.nu):
@@ -154,7 +158,7 @@ def adjoint(proj, vg, geom, wfun: int = 0, threads: int = 0, max_bytes: float = 
     rc = _load().gjp_oracle_adjoint(p.ctypes.data, *vg.n, h.ctypes.data, o.ctypes.data,
                                     geom.n_views, geom.nu, geom.nv, src.ctypes.data,
                                     org.ctypes.data, du.ctypes.data, dv.ctypes.data, int(wfun),
-                                    int(threads), float(max_bytes), out.ctypes.data)
+                                    float(fov), int(threads), float(max_bytes), out.ctypes.data)
     if rc:
         raise ValueError("gjp_oracle_adjoint failed")
     return out

@@ -64,7 +64,23 @@ typedef struct {
     double h[3];
     double origin[3];
     int wfun; /* 0 = w_lin (Eq. 13), 1 = w_spl (Eq. 14) */
+    double fov; /* > 0: sample only inside the cylinder of this radius (see below) */
 } oracle_volume;
+
+/*
+ * Field-of-view cylinder of the paper's speed benchmark: the sampling points
+ * of each ray are restricted to its intersection with a cylinder around the
+ * rotation axis (here: the line through the volume centre parallel to z, of
+ * world radius fov) instead of the bounding box.  A plane's sample p (index
+ * units) is kept iff its world distance from that axis is at most fov.
+ */
+static int outside_fov(const oracle_volume *V, const double p[3])
+{
+    if (!(V->fov > 0.0)) return 0;
+    const double dx = V->h[0] * (p[0] - 0.5 * (double)(V->n[0] - 1));
+    const double dy = V->h[1] * (p[1] - 0.5 * (double)(V->n[1] - 1));
+    return dx * dx + dy * dy > V->fov * V->fov;
+}
 
 static double vol_at(const oracle_volume *V, int64_t i, int64_t j, int64_t k)
 {
@@ -125,6 +141,7 @@ static double gjp_ray(const oracle_volume *V, const double s[3], const double d[
         double p[3], pfl[3], pcl[3], wfl[3], wcl[3];
         for (int k = 0; k < 3; ++k) p[k] = s[k] + (o + (double)i) * rt[k]; /* Eq. 6 */
         p[m] = (double)i;                                               /* C1 */
+        if (outside_fov(V, p)) continue;
         for (int k = 0; k < 3; ++k) {
             pfl[k] = floor(p[k]);                                       /* Eq. 7 */
             pcl[k] = ceil(p[k]);
@@ -190,10 +207,10 @@ static void set_threads(int nthreads)
 int gjp_oracle_forward(const void *vol, int vol_dtype, int64_t nx, int64_t ny, int64_t nz,
                        const double h[3], const double origin[3], int n_views, int nu, int nv,
                        const double *src, const double *det_origin, const double *det_u,
-                       const double *det_v, int wfun, int nthreads, double *proj)
+                       const double *det_v, int wfun, double fov, int nthreads, double *proj)
 {
     oracle_volume V = {vol, vol_dtype, {nx, ny, nz}, {h[0], h[1], h[2]},
-                       {origin[0], origin[1], origin[2]}, wfun};
+                       {origin[0], origin[1], origin[2]}, wfun, fov};
     if (check_volume(&V) || n_views < 0 || nu <= 0 || nv <= 0 || !proj) return 1;
     set_threads(nthreads);
     const int64_t n_rays = (int64_t)n_views * nv * nu;
@@ -217,10 +234,10 @@ int gjp_oracle_rays(const void *vol, int vol_dtype, int64_t nx, int64_t ny, int6
                     const double h[3], const double origin[3], const double *src,
                     const double *det_origin, const double *det_u, const double *det_v,
                     int64_t n_rays, const int32_t *view, const int32_t *iu, const int32_t *iv,
-                    const int32_t *axis, int wfun, int nthreads, double *out)
+                    const int32_t *axis, int wfun, double fov, int nthreads, double *out)
 {
     oracle_volume V = {vol, vol_dtype, {nx, ny, nz}, {h[0], h[1], h[2]},
-                       {origin[0], origin[1], origin[2]}, wfun};
+                       {origin[0], origin[1], origin[2]}, wfun, fov};
     if (check_volume(&V) || n_rays < 0 || !out) return 1;
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -245,7 +262,7 @@ int gjp_oracle_ray_info(int64_t nx, int64_t ny, int64_t nz, const double h[3], c
                         double *margin_out)
 {
     oracle_volume V = {NULL, -1, {nx, ny, nz}, {h[0], h[1], h[2]},
-                       {origin[0], origin[1], origin[2]}, 0};
+                       {origin[0], origin[1], origin[2]}, 0, 0.0};
     for (int64_t j = 0; j < n_rays; ++j) {
         double s[3], d[3], r[3], a[3];
         ray_endpoints(&V, src, det_origin, det_u, det_v, view[j], iu[j], iv[j], s, d);
@@ -273,10 +290,10 @@ int gjp_oracle_ray_info(int64_t nx, int64_t ny, int64_t nz, const double h[3], c
 int gjp_oracle_adjoint(const double *proj, int64_t nx, int64_t ny, int64_t nz, const double h[3],
                        const double origin[3], int n_views, int nu, int nv, const double *src,
                        const double *det_origin, const double *det_u, const double *det_v,
-                       int wfun, int nthreads, double max_bytes, double *vol_out)
+                       int wfun, double fov, int nthreads, double max_bytes, double *vol_out)
 {
     oracle_volume V = {NULL, -1, {nx, ny, nz}, {h[0], h[1], h[2]},
-                       {origin[0], origin[1], origin[2]}, wfun};
+                       {origin[0], origin[1], origin[2]}, wfun, fov};
     for (int k = 0; k < 3; ++k)
         if (V.n[k] <= 0 || !(V.h[k] > 0.0)) return 1;
     if (!proj || !vol_out || n_views < 0 || nu <= 0 || nv <= 0) return 1;

@@ -61,6 +61,14 @@ class Geometry:
         if st != _capi.GJP_OK:
             raise GjpError(st, "gjp_geometry_set_launch")
 
+    def set_fov(self, radius: float):
+        """Clip every ray to the cylinder of world ``radius`` around the axis
+        through the volume centre parallel to z (0 turns it off)."""
+        st = _capi.gjp_geometry_set_fov(self.handle, radius)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_geometry_set_fov")
+        self.fov = float(radius)
+
     @property
     def launch(self):
         st, tu, vg = _capi.gjp_geometry_get_launch(self.handle)

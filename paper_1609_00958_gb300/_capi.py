@@ -39,7 +39,7 @@ GJP_PATH_HWLIN = 6
 
 #: every symbol include/gjp.h declares
 EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_geometry_set_weight",
-           "gjp_geometry_set_launch", "gjp_geometry_get_launch", "gjp_forward",
+           "gjp_geometry_set_launch", "gjp_geometry_get_launch", "gjp_geometry_set_fov", "gjp_forward",
            "gjp_forward_ex", "gjp_forward_noalloc", "gjp_stream_status", "gjp_adjoint", "gjp_adjoint_ex",
            "gjp_footprint", "gjp_batch_create", "gjp_batch_destroy", "gjp_batch_forward",
            "gjp_batch_autotune", "gjp_batch_get_tuning", "gjp_batch_set_tuning", "gjp_status_string")
@@ -89,6 +89,8 @@ def load(path: str | None = None):
     lib.gjp_geometry_set_launch.restype = _I
     lib.gjp_geometry_get_launch.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]
     lib.gjp_geometry_get_launch.restype = _I
+    lib.gjp_geometry_set_fov.argtypes = [_P, ctypes.c_double]
+    lib.gjp_geometry_set_fov.restype = _I
     lib.gjp_forward.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _P]
     lib.gjp_forward.restype = _I
     lib.gjp_forward_ex.argtypes = [_P, _I, _I64, _I64, _I64, _D3, _D3, _P, _P, _I, _P]
@@ -169,6 +171,10 @@ def gjp_geometry_set_weight(handle, weight: int) -> int:
 
 def gjp_geometry_set_launch(handle, tile_u: int, view_group: int) -> int:
     return load().gjp_geometry_set_launch(_P(handle) if handle else None, int(tile_u), int(view_group))
+
+
+def gjp_geometry_set_fov(handle, radius: float) -> int:
+    return load().gjp_geometry_set_fov(_P(handle) if handle else None, float(radius))
 
 
 def gjp_geometry_get_launch(handle):

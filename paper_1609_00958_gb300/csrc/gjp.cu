@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_kernel(
 // does not depend on how the rays are spaced.  This halves the reductions
 // of the tap-by-tap scatter.  Warps without a common row scatter tap by tap.
 
-template <typename Index, bool SPL>
+template <typename Index, bool SPL, bool CLIP>
 __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views,
     int nu, int nv, int n_tv, int n_views, int view_group, float *__restrict__ vol)
@@ -651,7 +651,8 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
 
     // m in {x, y}: b is z (stride 1); a, ia and da are the same on every
     // lane.  Planes outside a lane's support put its taps outside the grid,
-    // where the zero-border checks drop them.
+    // where the zero-border checks drop them -- unless the rays are clipped
+    // to a field-of-view cylinder (CLIP), where the plane test is explicit.
     const float yw = act ? ys : 0.0f;
     const Index sa = (Index)R.sa, sm = (Index)R.sm;
     const unsigned na = (unsigned)R.na, nb = (unsigned)R.nb;
@@ -662,8 +663,9 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     for (int i = I0; i <= I1; ++i) {
         const int ia = floor_of(pa), ib = floor_of(pb);
         const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
-        const float g1 = yw * db;                      // to voxel ib + 1
-        const float g0 = __fmaf_rn(-yw, db, yw);       // yw (1 - db), to voxel ib
+        const float yi = (!CLIP || (i >= R.s_lo && i <= R.s_hi)) ? yw : 0.0f;
+        const float g1 = yi * db;                      // to voxel ib + 1
+        const float g0 = __fmaf_rn(-yi, db, yi);       // yi (1 - db), to voxel ib
         // the previous lane's upper tap joins this lane's lower tap when they
         // are the same voxel (lane 0 receives its own values: never taken)
         const int ib_up = __shfl_up_sync(full, ib, 1);
@@ -949,9 +951,10 @@ gjp_status check_sources(const gjp_geometry *g, const int64_t n[3], const double
     return GJP_OK;
 }
 
-VolParams make_vol(const int64_t n[3], const double h[3])
+VolParams make_vol(const int64_t n[3], const double h[3], double fov)
 {
     VolParams V;
+    V.fov_r2 = fov > 0.0 ? (float)(fov * fov) : 0.0f;
     for (int k = 0; k < 3; ++k) {
         V.n[k] = (int)n[k];
         V.h[k] = (float)h[k];
@@ -1196,7 +1199,7 @@ gjp_status forward_typed(const void *d_volume, gjp_dtype dt, const int64_t n[3],
                          const double o[3], const gjp_geometry &g, gjp_cache_entry &entry, float *proj,
                          int path, cudaStream_t s)
 {
-    const VolParams V = make_vol(n, h);
+    const VolParams V = make_vol(n, h, g.fov);
     const bool i32 = fits_int32(n);
     const T *vol = static_cast<const T *>(d_volume);
     const ViewParams *table = entry.d_table;
@@ -1273,7 +1276,7 @@ bool try_adjoint_slab(const float *proj, const int64_t n[3], const double h[3], 
     const SlabPlan p = slab_plan(bs, vol, GJP_F32, n);
     CUtensorMap mx, my;
     if (!p.ok || !encode_maps(vol, GJP_F32, n, p.rows, p.cols, &mx, &my)) return false;
-    const VolParams V = make_vol(n, h);
+    const VolParams V = make_vol(n, h, g.fov);
     const bool i32 = fits_int32(n);
     if (p.cols == 48)
         err = i32 ? launch_adjoint_slab<int, 48>(proj, V, entry.d_table, g, mx, my, p.rows, vol, s)
@@ -1416,6 +1419,13 @@ gjp_status gjp_geometry_set_launch(gjp_geometry *g, int tile_u, int view_group)
     return GJP_OK;
 }
 
+gjp_status gjp_geometry_set_fov(gjp_geometry *g, double radius)
+{
+    if (!g || !std::isfinite(radius) || radius < 0.0) return GJP_ERR_INVALID_ARG;
+    g->fov = radius;
+    return GJP_OK;
+}
+
 gjp_status gjp_geometry_get_launch(const gjp_geometry *g, int *tile_u, int *view_group)
 {
     if (!g) return GJP_ERR_INVALID_ARG;
@@ -1519,7 +1529,7 @@ gjp_status gjp_forward_noalloc(const void *d_volume, gjp_dtype dtype, int64_t nx
             cudaSuccess)
             return GJP_ERR_CUDA;
     }
-    const VolParams V = make_vol(n, h);
+    const VolParams V = make_vol(n, h, g->fov);
     const bool i32 = fits_int32(n);
     cudaError_t e = cudaSuccess;
     switch (dtype) {
@@ -1569,27 +1579,26 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
     const bool spl = g->weight == GJP_WEIGHT_SPL;
     if (path == GJP_PATH_SLAB && spl) return GJP_ERR_UNSUPPORTED;   // the slab adjoint implements w_lin only
     if (path == GJP_PATH_COMBINE || (path == GJP_PATH_AUTO && GJP_ADJOINT_AUTO == GJP_PATH_COMBINE)) {
-        const VolParams V = make_vol(n, h);
+        const VolParams V = make_vol(n, h, g->fov);
         const int n_tv = (g->nv + kTileV - 1) / kTileV;
         const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
         const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
         const dim3 block(kTileV, g->tile_u);
         const int nvw = g->n_views, vgp = g->view_group;
+        const bool clip = V.fov_r2 > 0.0f;
+#define GJP_COMBINE_LAUNCH(I, S, C)                                                                                \
+    gjp_adjoint_combine_kernel<I, S, C><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw, vgp, d_volume)
         if (fits_int32(n)) {
-            if (spl)
-                gjp_adjoint_combine_kernel<int, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw,
-                                                                            vgp, d_volume);
-            else
-                gjp_adjoint_combine_kernel<int, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv,
-                                                                             nvw, vgp, d_volume);
+            if (spl) { if (clip) GJP_COMBINE_LAUNCH(int, true, true); else GJP_COMBINE_LAUNCH(int, true, false); }
+            else { if (clip) GJP_COMBINE_LAUNCH(int, false, true); else GJP_COMBINE_LAUNCH(int, false, false); }
         } else {
-            if (spl)
-                gjp_adjoint_combine_kernel<long long, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv,
-                                                                                  n_tv, nvw, vgp, d_volume);
-            else
-                gjp_adjoint_combine_kernel<long long, false><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv,
-                                                                                   n_tv, nvw, vgp, d_volume);
+            if (spl) {
+                if (clip) GJP_COMBINE_LAUNCH(long long, true, true); else GJP_COMBINE_LAUNCH(long long, true, false);
+            } else {
+                if (clip) GJP_COMBINE_LAUNCH(long long, false, true); else GJP_COMBINE_LAUNCH(long long, false, false);
+            }
         }
+#undef GJP_COMBINE_LAUNCH
         return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
     }
     if (path != GJP_PATH_GATHER && !spl) {
@@ -1598,7 +1607,7 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
             return e == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
         if (path == GJP_PATH_SLAB) return GJP_ERR_UNSUPPORTED;
     }
-    const VolParams V = make_vol(n, h);
+    const VolParams V = make_vol(n, h, g->fov);
     const int n_tv = (g->nv + kTileV - 1) / kTileV;
     const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
@@ -1641,7 +1650,7 @@ gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny
     gjp_cache_entry *entry = nullptr;
     if ((st = get_table(g, n, h, o, &entry)) != GJP_OK) return st;
     const ViewParams *table = entry->d_table;
-    const VolParams V = make_vol(n, h);
+    const VolParams V = make_vol(n, h, g->fov);
     const int n_tv = (g->nv + kTileV - 1) / kTileV;
     const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
     const dim3 grid((unsigned)(n_tv * n_tu));

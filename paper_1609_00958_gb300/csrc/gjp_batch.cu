@@ -249,7 +249,7 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
         P.vol = q.d_volume;
         P.proj = q.d_proj;
         P.table = entry->d_table;
-        P.V = make_vol(n, h);
+        P.V = make_vol(n, h, q.geometry->fov);
         P.nu = q.geometry->nu;
         P.nv = q.geometry->nv;
         P.kind = (int)q.dtype | (fits_int32(n) ? 4 : 0) | (q.geometry->weight == GJP_WEIGHT_SPL ? 8 : 0);

@@ -37,6 +37,7 @@ struct VolParams {
     int n[3];
     float h[3];         // voxel size (world)
     long long s[3];     // element strides: ny*nz, nz, 1
+    float fov_r2;       // > 0: squared world radius of the field-of-view cylinder (rays clipped to it)
 };
 
 #ifndef GJP_TILE_U
@@ -79,6 +80,7 @@ struct gjp_cache_entry {
 struct gjp_geometry {
     int n_views, nu, nv;
     int weight = GJP_WEIGHT_LIN;          // interpolation weight function (Eq. 13 or Eq. 14)
+    double fov = 0.0;                     // > 0: field-of-view cylinder radius (world units)
     int tile_u = gjp_detail::kTileU;                  // launch shape: warps (detector columns) per block
     int view_group = GJP_VIEW_GROUP;      // launch order: views interleaved per detector tile
     std::vector<double> src, org, du, dv;
@@ -102,7 +104,7 @@ gjp_status check_grid(int64_t nx, int64_t ny, int64_t nz, const double h[3], con
                       int64_t n[3], double hh[3], double o[3]);
 // Rejects a geometry with a source inside the interpolated support of the grid.
 gjp_status check_sources(const gjp_geometry *g, const int64_t n[3], const double h[3], const double o[3]);
-VolParams make_vol(const int64_t n[3], const double h[3]);
+VolParams make_vol(const int64_t n[3], const double h[3], double fov);
 // Whether every element offset the kernels form fits a signed 32-bit integer.
 bool fits_int32(const int64_t n[3]);
 size_t elem_size(gjp_dtype t);
@@ -256,6 +258,50 @@ __device__ __forceinline__ void plane_interval(long long P, long long G, int ic,
     }
 }
 
+// Field-of-view cylinder (the speed section samples each ray only on its
+// intersection with a cylinder around the rotation axis): keeps the planes
+// whose sample lies within world radius sqrt(fov_r2) of the axis through
+// the volume centre parallel to z.  The sample's (x, y) is affine in the
+// plane index t = i - ic, so the kept planes are the integers between the
+// two roots of a quadratic (float32; a sample within ~1e-4 plane of the
+// circle may fall on either side, which cannot matter for a volume that is
+// zero near the cylinder wall, the setting this option is for).
+__device__ __forceinline__ void clip_to_fov(const VolParams &V, Ray &R, int m)
+{
+    const float inv = 2.3283064365386963e-10f;   // 2^-32
+    // index position at t = 0 and per plane, for x and y
+    float p0[2], dp[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool is_m = k == m, is_a = k == ((m == 0) ? 1 : 0);
+        p0[k] = is_m ? (float)R.ic : __ll2float_rn(is_a ? R.Pa : R.Pb) * inv;
+        dp[k] = is_m ? 1.0f : __ll2float_rn(is_a ? R.Ga : R.Gb) * inv;
+    }
+    const float X0 = V.h[0] * (p0[0] - 0.5f * (float)(V.n[0] - 1)), dX = V.h[0] * dp[0];
+    const float Y0 = V.h[1] * (p0[1] - 0.5f * (float)(V.n[1] - 1)), dY = V.h[1] * dp[1];
+    const float A = dX * dX + dY * dY, B = X0 * dX + Y0 * dY, C = X0 * X0 + Y0 * Y0 - V.fov_r2;
+    int lo, hi;
+    if (A <= 0.0f) {                       // no motion in (x, y): all planes or none
+        lo = C <= 0.0f ? 0 : 1;
+        hi = C <= 0.0f ? 0x3fffffff : 0;
+    } else {
+        const float disc = B * B - A * C;
+        if (disc < 0.0f) {
+            lo = 1;
+            hi = 0;
+        } else {
+            const float sq = sqrtf(disc);
+            const float t1 = (-B - sq) / A, t2 = (-B + sq) / A;
+            lo = R.ic + (int)ceilf(fmaxf(t1, -1.0e9f));
+            hi = R.ic + (int)floorf(fminf(t2, 1.0e9f));
+        }
+    }
+    R.s_lo = max(R.s_lo, lo);
+    R.s_hi = min(R.s_hi, hi);
+    R.j_lo = max(R.j_lo, lo);
+    R.j_hi = min(R.j_hi, hi);
+}
+
 __device__ __forceinline__ void setup_ray(const ViewParams &vp, const VolParams &V, float u, float v, Ray &R)
 {
     const f2 r0 = f2_affine(vp.rh, vp.rl, 0, u, v);
@@ -309,6 +355,7 @@ __device__ __forceinline__ void setup_ray(const ViewParams &vp, const VolParams 
     R.s_hi = min(sa1, sb1);
     R.j_lo = max(max(ja0, jb0), R.s_lo);
     R.j_hi = min(min(ja1, jb1), R.s_hi);
+    if (V.fov_r2 > 0.0f) clip_to_fov(V, R, m);
 }
 
 __device__ __forceinline__ void load_view(const ViewParams *__restrict__ views, int k, ViewParams &vp)

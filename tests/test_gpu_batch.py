@@ -174,3 +174,18 @@ def test_c5_batching_workload(gjp):
         scale = max(np.abs(oref).max(), float(out.abs().max()))
         parity.check_rays(got, stored, vg, cg, *rays, scale, TOL32, ref=oref)
         del ref
+
+
+def test_batch_respects_field_of_view(gjp):
+    """A geometry clipped to a field-of-view cylinder projects the same way
+    batched and alone."""
+    probs = _small_problems(gjp)[:3]
+    items = _batch_inputs(gjp, probs)
+    items[2][1].set_fov(12.0)
+    batch = gjp.Batch(items)
+    batch.forward()
+    gjp.stream_status()
+    for vol, g, h, origin, out in items:
+        assert torch.equal(out, gjp.forward(vol, g, h, origin))
+    assert not torch.equal(items[2][4], gjp.forward(items[2][0], gjp.Geometry.from_cone(probs[2][3]),
+                                                    items[2][2], items[2][3]))

@@ -391,3 +391,57 @@ def test_linear_weights_beat_spline_weights_against_analytic_projections():
         e_lin = np.abs(oracle.forward(vol, vg, g, wfun=0) - pa).sum() / np.abs(pa).sum()
         e_spl = np.abs(oracle.forward(vol, vg, g, wfun=1) - pa).sum() / np.abs(pa).sum()
         assert e_lin < e_spl, (n, e_lin, e_spl)
+
+
+# --- field-of-view cylinder of the speed section: sampling restricted to
+# the ray-cylinder intersection instead of the bounding box ------------------
+
+def _cylinder_mask(vg, radius):
+    """True where a voxel centre lies within world distance `radius` of the
+    axis through the volume centre parallel to z."""
+    x = (np.arange(vg.n[0]) - 0.5 * (vg.n[0] - 1)) * vg.h[0]
+    y = (np.arange(vg.n[1]) - 0.5 * (vg.n[1] - 1)) * vg.h[1]
+    return (x[:, None] ** 2 + y[None, :] ** 2 <= radius ** 2)[:, :, None]
+
+
+def test_fov_clipping_changes_nothing_inside_the_cylinder():
+    """A volume that is zero farther than R - 2 voxels from the axis has no
+    non-zero tap at a sample outside radius R (taps reach one voxel along
+    each transverse axis), so clipping the rays to the cylinder of radius R
+    changes no projection; a cylinder that contains the box changes none
+    either, and a small one does change them."""
+    rng = _rng(81)
+    vg = VolumeGeometry.centred((24, 22, 10), h=(1.0, 1.1, 0.9))
+    r = 9.0
+    vol = rng.random(vg.n) * _cylinder_mask(vg, r - 2.5)
+    g = synth.circular(5, 31, 12, 80.0, 160.0, 1.2, angles=[0.1, 0.9, 1.6, 2.8, 4.4])
+    full = oracle.forward(vol, vg, g)
+    np.testing.assert_allclose(oracle.forward(vol, vg, g, fov=r), full, rtol=0, atol=1e-12 * np.abs(full).max())
+    np.testing.assert_allclose(oracle.forward(vol, vg, g, fov=100.0), full, rtol=0, atol=0)
+    assert np.abs(oracle.forward(vol, vg, g, fov=r - 5.0) - full).max() > 1e-2 * np.abs(full).max()
+
+
+def test_fov_clipped_constant_volume_counts_the_planes_in_the_cylinder():
+    """An axis-aligned ray along x through voxel centres of a constant volume
+    samples, with clipping, exactly the planes i with h_x |i - c_x| <= R:
+    the result is h_x times that count (and the full column without it)."""
+    vg = VolumeGeometry.centred((21, 9, 7), h=(0.5, 1.0, 1.0))
+    vol = np.ones(vg.n)
+    centre = np.array(vg.origin) + np.array([10, 4, 3]) * np.array(vg.h)
+    g = _single_ray_geometry(centre - np.array([50.0, 0, 0]), centre + np.array([50.0, 0, 0]))
+    for radius in (1.0, 2.26, 3.0, 20.0):
+        count = sum(1 for i in range(vg.n[0]) if abs(vg.h[0] * (i - 10)) <= radius)
+        got = oracle.forward(vol, vg, g, fov=radius)[0, 0, 0]
+        assert got == pytest.approx(vg.h[0] * count, rel=1e-14), radius
+
+
+def test_fov_clipped_adjoint_is_the_transpose():
+    rng = _rng(82)
+    vg = VolumeGeometry.centred((12, 11, 9))
+    g = synth.random_geometry(rng, vg, 3, 9, 8)
+    x = rng.standard_normal(vg.n)
+    y = rng.standard_normal((g.n_views, g.nv, g.nu))
+    lhs = np.sum(oracle.forward(x, vg, g, fov=4.5) * y)
+    rhs = np.sum(x * oracle.adjoint(y, vg, g, fov=4.5))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    assert abs(lhs - np.sum(oracle.forward(x, vg, g) * y)) > 1e-3 * abs(lhs)
