@@ -209,6 +209,17 @@ gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int
 gjp_status gjp_stream_status(void *stream);
 
 /*
+ * gjp_selftest_wait_timeout -- failure-detection self-test (the paper has
+ * no counterpart): launches on `stream` one kernel whose thread waits,
+ * through the same bounded wait as the library's pipelines, on a barrier
+ * phase that nothing ever completes.  The wait gives up after its limit
+ * (one second of wall time), the kernel records the timeout and returns,
+ * and the next gjp_stream_status(stream) reports GJP_ERR_TIMEOUT; the GPU
+ * context stays usable.  Touches no caller memory.
+ */
+gjp_status gjp_selftest_wait_timeout(void *stream);
+
+/*
  * gjp_adjoint -- matched transpose of gjp_forward (float32 volume):
  * d_volume (+)= A^T d_proj, where A is the system matrix of gjp_forward
  * (the g = A f view of the reconstruction section).  Every (ray, plane,

@@ -192,13 +192,43 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 
-// Bounded wait: false (and the status word set) if the phase never completes.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false (and the status word set) if the phase has not
+// completed after kSpinLimit polls or kWaitLimitNs of wall time, whichever
+// comes first (try_wait may suspend the thread between polls for a
+// hardware-defined time, so the clock bounds the wait, not the count).
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
 {
-    for (unsigned spin = 0; spin < kSpinLimit; ++spin)
+    const unsigned long long t0 = global_ns();
+    for (unsigned spin = 0; spin < kSpinLimit; ++spin) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) break;
+    }
     atomicOr(&g_gjp_status, 1u);
     return false;
+}
+
+// Failure-detection self-test: one thread waits, through the same bounded
+// wait as the pipelines, on an mbarrier phase that nothing completes (the
+// barrier expects one arrival and none comes).  The wait gives up after its
+// limit, sets the status word and the kernel returns; no memory other than
+// its own shared word is touched.
+__global__ void gjp_wait_selftest_kernel()
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait(&bar, 0);
+    }
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, unsigned long long *bar, int c0,
@@ -1540,6 +1570,12 @@ gjp_status gjp_forward_noalloc(const void *d_volume, gjp_dtype dtype, int64_t nx
     case GJP_F16: e = launch_gather<__half>((const __half *)d_volume, V, d_table, *g, i32, d_proj, s); break;
     }
     return e == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+}
+
+gjp_status gjp_selftest_wait_timeout(void *stream)
+{
+    gjp_wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>();
+    return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
 gjp_status gjp_stream_status(void *stream)

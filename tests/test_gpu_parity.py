@@ -707,3 +707,26 @@ def test_fov_argument_checks(gjp):
         with pytest.raises(gjp.GjpError):
             g.set_fov(bad)
     g.set_fov(0.0)
+
+
+def test_bounded_wait_times_out_and_is_reported(gjp):
+    """Failure detection without a fault: a kernel waits, through the
+    library's bounded wait, on a barrier phase that nothing completes.  The
+    wait gives up after its limit, gjp_stream_status reports
+    GJP_ERR_TIMEOUT once (the flag is then cleared), and the context keeps
+    working."""
+    import time
+    from paper_1609_00958_gb300 import _capi
+    stream = torch.cuda.current_stream().cuda_stream
+    gjp.stream_status()                                 # nothing pending
+    t0 = time.perf_counter()
+    assert _capi.gjp_selftest_wait_timeout(stream) == _capi.GJP_OK
+    assert _capi.gjp_stream_status(stream) == _capi.GJP_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    assert _capi.gjp_stream_status(stream) == _capi.GJP_OK
+    vg, cg = synth.c1_geometry()
+    vol = synth.voxelize(vg, supersample=2)
+    out = gjp.forward(torch.from_numpy(vol).cuda(), gjp.Geometry.from_cone(cg.subset([0, 9])), vg.h)
+    gjp.stream_status()
+    ref = oracle.forward(vol, vg, cg.subset([0, 9]))
+    assert np.abs(out.cpu().numpy() - ref).max() <= TOL32 * np.abs(ref).max()
