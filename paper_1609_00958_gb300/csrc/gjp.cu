@@ -643,6 +643,55 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_kernel(
 // does not depend on how the rays are spaced.  This halves the reductions
 // of the tap-by-tap scatter.  Warps without a common row scatter tap by tap.
 
+// One plane of the warp-combined adjoint (see above).  CHECKED tests each
+// tap against the grid (zero border) and, with CLIP, the plane against the
+// ray's clipped support; unchecked planes are interior for every lane.
+template <typename Index, bool SPL, bool CHECKED, bool CLIP>
+__device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, unsigned long long &pa,
+                                              unsigned long long &pb, Index &plane, Index sa, unsigned na,
+                                              unsigned nb, float *__restrict__ vol)
+{
+    const unsigned full = 0xffffffffu;
+    const int ia = floor_of(pa), ib = floor_of(pb);
+    const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
+    const float yi = (!CLIP || (i >= R.s_lo && i <= R.s_hi)) ? yw : 0.0f;
+    const float g1 = yi * db;                      // to voxel ib + 1
+    const float g0 = __fmaf_rn(-yi, db, yi);       // yi (1 - db), to voxel ib
+    // the previous lane's upper tap joins this lane's lower tap when they
+    // are the same voxel (lane 0 receives its own values: never taken)
+    const int ib_up = __shfl_up_sync(full, ib, 1);
+    const float g1_up = __shfl_up_sync(full, g1, 1);
+    const int ib_dn = __shfl_down_sync(full, ib, 1);
+    const float x0 = ib_up + 1 == ib ? g0 + g1_up : g0;
+    const float x1 = ib_dn == ib + 1 ? 0.0f : g1;    // kept when the next lane does not take it
+    float *p = vol + (plane + (Index)ia * sa + (Index)ib);
+    const float wa0 = 1.0f - da;
+    if (CHECKED) {
+        const bool r0 = (unsigned)ia < na, r1 = (unsigned)(ia + 1) < na;   // zero border
+        const bool z0 = (unsigned)ib < nb, z1 = (unsigned)(ib + 1) < nb;
+        if (z0 && x0 != 0.0f) {
+            if (r0) atomicAdd(p, wa0 * x0);
+            if (r1) atomicAdd(p + sa, da * x0);
+        }
+        if (z1 && x1 != 0.0f) {
+            if (r0) atomicAdd(p + 1, wa0 * x1);
+            if (r1) atomicAdd(p + sa + 1, da * x1);
+        }
+    } else {
+        if (x0 != 0.0f) {
+            atomicAdd(p, wa0 * x0);
+            atomicAdd(p + sa, da * x0);
+        }
+        if (x1 != 0.0f) {
+            atomicAdd(p + 1, wa0 * x1);
+            atomicAdd(p + sa + 1, da * x1);
+        }
+    }
+    pa += (unsigned long long)R.Ga;
+    pb += (unsigned long long)R.Gb;
+    plane += (Index)R.sm;
+}
+
 template <typename Index, bool SPL, bool CLIP>
 __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views,
@@ -688,37 +737,23 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     const unsigned na = (unsigned)R.na, nb = (unsigned)R.nb;
     unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, I0, R.ic);
     unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, I0, R.ic);
-    const unsigned long long ga = (unsigned long long)R.Ga, gb = (unsigned long long)R.Gb;
     Index plane = (Index)I0 * sm;
-    for (int i = I0; i <= I1; ++i) {
-        const int ia = floor_of(pa), ib = floor_of(pb);
-        const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
-        const float yi = (!CLIP || (i >= R.s_lo && i <= R.s_hi)) ? yw : 0.0f;
-        const float g1 = yi * db;                      // to voxel ib + 1
-        const float g0 = __fmaf_rn(-yi, db, yi);       // yi (1 - db), to voxel ib
-        // the previous lane's upper tap joins this lane's lower tap when they
-        // are the same voxel (lane 0 receives its own values: never taken)
-        const int ib_up = __shfl_up_sync(full, ib, 1);
-        const float g1_up = __shfl_up_sync(full, g1, 1);
-        const int ib_dn = __shfl_down_sync(full, ib, 1);
-        const float x0 = ib_up + 1 == ib ? g0 + g1_up : g0;
-        const float x1 = ib_dn == ib + 1 ? 0.0f : g1;    // kept when the next lane does not take it
-        const bool r0 = (unsigned)ia < na, r1 = (unsigned)(ia + 1) < na;   // zero border
-        const bool z0 = (unsigned)ib < nb, z1 = (unsigned)(ib + 1) < nb;
-        float *p = vol + (plane + (Index)ia * sa + (Index)ib);
-        const float wa0 = 1.0f - da;
-        if (z0 && x0 != 0.0f) {
-            if (r0) atomicAdd(p, wa0 * x0);
-            if (r1) atomicAdd(p + sa, da * x0);
-        }
-        if (z1 && x1 != 0.0f) {
-            if (r0) atomicAdd(p + 1, wa0 * x1);
-            if (r1) atomicAdd(p + sa + 1, da * x1);
-        }
-        pa += ga;
-        pb += gb;
-        plane += sm;
+
+    // Planes F0 .. F1 are interior for every lane of the warp (ghost lanes
+    // included: their rays are real rays beyond the detector edge): all
+    // four taps of every lane lie in the grid and in the support, so they
+    // run without checks; the planes before and after check each tap.
+    const int F0 = __reduce_max_sync(full, R.j_lo), F1 = __reduce_min_sync(full, R.j_hi);
+    const int c_end = F0 <= F1 ? min(F0, I1 + 1) : I1 + 1;
+    int i = I0;
+    for (; i < c_end; ++i)
+        combine_plane<Index, SPL, true, CLIP>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+    if (F0 <= F1) {
+        for (; i <= min(F1, I1); ++i)
+            combine_plane<Index, SPL, false, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
     }
+    for (; i <= I1; ++i)
+        combine_plane<Index, SPL, true, CLIP>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
 }
 
 // ---------------------------------------------------------------------------
