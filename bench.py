@@ -392,7 +392,12 @@ def run_gjp(args):
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(args, vg, cg, vol_np, counts, budget_s=args.cpu_seconds)
+        sample_views = list(range(0, cg.n_views, max(1, cg.n_views // 36)))
+        gpu_views = {v: (proj32[v].cpu().numpy(), proj16[v].cpu().numpy()) for v in sample_views}
+        result["cpu_baseline"] = cpu_baseline(args, vg, cg, vol_np, counts, budget_s=args.cpu_seconds,
+                                              gpu_views=gpu_views)
+        if "error_vs_oracle" in result["cpu_baseline"]:
+            result["error_vs_oracle"] = result["cpu_baseline"]["error_vs_oracle"]
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -468,13 +473,17 @@ def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step):
 
 # --- CPU oracle (baseline leg and reference arm) ----------------------------------
 
-def oracle_step(oracle, vg, cg, vol_np, vol_bf16w, view, threads, counts):
+def oracle_step(oracle, vg, cg, vol_np, vol_bf16w, view, threads, counts, keep=None):
+    """One view of the step on the oracle (forward f32, forward of the
+    bfloat16-stored values, adjoint); `keep` collects the two projections."""
     sub = cg.subset([view])
     t0 = time.perf_counter()
     p = oracle.forward(vol_np, vg, sub, threads=threads)
-    oracle.forward(vol_bf16w, vg, sub, threads=threads)
+    p16 = oracle.forward(vol_bf16w, vg, sub, threads=threads)
     oracle.adjoint(p, vg, sub, threads=threads, max_bytes=16e9)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep[view] = (p[0], p16[0])
     return dt, 3 * int(counts[view])
 
 
@@ -485,23 +494,44 @@ def bf16_widened(vol_np):
     return torch.from_numpy(vol_np).to(torch.bfloat16).float().numpy()
 
 
-def cpu_baseline(args, vg, cg, vol_np, counts, budget_s):
+def cpu_baseline(args, vg, cg, vol_np, counts, budget_s, gpu_views=None):
+    """The oracle timed on the host cores over a time-bounded sample of
+    views.  With `gpu_views` (view -> (float32 projection, bfloat16
+    projection) from the timed GPU step), the same oracle projections also
+    give the GPU results' error on those views: max and RMS |gpu - oracle|
+    relative to the oracle maximum, against the float32 volume and, for
+    bfloat16 storage, also against the stored (rounded) values."""
     import oracle
     threads = os.cpu_count() or 1
     vol_w = bf16_widened(vol_np)
     views = list(range(0, cg.n_views, max(1, cg.n_views // 36)))
-    t_tot, s_tot, used = 0.0, 0, []
+    t_tot, s_tot, used, kept = 0.0, 0, [], {}
     for v in views:
-        dt, s = oracle_step(oracle, vg, cg, vol_np, vol_w, v, threads, counts)
+        dt, s = oracle_step(oracle, vg, cg, vol_np, vol_w, v, threads, counts, keep=kept)
         t_tot += dt
         s_tot += s
         used.append(v)
         if t_tot >= budget_s:
             break
-    return {"value": round(s_tot / t_tot / 1e9, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"FP64 oracle (OpenMP, {threads} threads) on {len(used)} of {cg.n_views} views "
-                      f"(views {used[0]}..{used[-1]} step {views[1] - views[0] if len(views) > 1 else 0}): "
-                      "forward f32 + forward bf16-stored + adjoint per view, same volume and geometry"}
+    out = {"value": round(s_tot / t_tot / 1e9, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"FP64 oracle (OpenMP, {threads} threads) on {len(used)} of {cg.n_views} views "
+                     f"(views {used[0]}..{used[-1]} step {views[1] - views[0] if len(views) > 1 else 0}): "
+                     "forward f32 + forward bf16-stored + adjoint per view, same volume and geometry"}
+    if gpu_views:
+        def err(gpu, ref):
+            d = np.abs(np.asarray(gpu, np.float64) - ref)
+            m = max(float(np.abs(ref).max()), 1e-30)
+            return {"max_rel": float(f"{d.max() / m:.3e}"), "rms_rel": float(f"{np.sqrt(np.mean(d * d)) / m:.3e}")}
+        e32 = [err(gpu_views[v][0], kept[v][0]) for v in used]
+        e16 = [err(gpu_views[v][1], kept[v][0]) for v in used]
+        e16s = [err(gpu_views[v][1], kept[v][1]) for v in used]
+        worst = lambda es: {"max_rel": max(e["max_rel"] for e in es),
+                            "rms_rel": float(f"{np.sqrt(np.mean([e['rms_rel'] ** 2 for e in es])):.3e}")}
+        out["error_vs_oracle"] = {
+            "views": used, "forward_f32": worst(e32), "forward_bf16": worst(e16),
+            "forward_bf16_vs_stored_values": worst(e16s),
+            "bounds": {"f32": 1e-5, "bf16": 5e-3, "bf16_vs_stored_values": 1e-5}}
+    return out
 
 
 def run_reference(args):
