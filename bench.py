@@ -57,6 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--views", type=int, default=360)
     p.add_argument("--first-views", type=int, default=0,
                    help="keep only the first K views of the --views geometry (small profiling captures)")
+    p.add_argument("--forward-path", choices=["auto", "gather", "slab", "prefetch", "texture", "hwlin"],
+                   default="auto", help="forward kernel family of the step (profiling other families)")
     p.add_argument("--tile-u", type=int, default=None, help="detector columns per block (library default if unset)")
     p.add_argument("--view-group", type=int, default=None, help="views issued together (library default if unset)")
     p.add_argument("--content", choices=["random", "phantom"], default="random")
@@ -298,7 +300,10 @@ def run_gjp(args):
 
     vol_np = make_volume(args, vg, seed=rank)
     vol32 = torch.from_numpy(vol_np).to(dev)
-    vol16 = vol32.to(torch.bfloat16)
+    # the texture unit has no bfloat16 format: the texture families store the 16-bit form as float16
+    tex = args.forward_path in ("texture", "hwlin")
+    vol16 = vol32.to(torch.float16 if tex else torch.bfloat16)
+    k16 = "forward_f16" if tex else "forward_bf16"
     proj32 = torch.empty(cg.n_views, cg.nv, cg.nu, device=dev)
     proj16 = torch.empty_like(proj32)
     back = torch.empty(vg.n, device=dev)
@@ -310,19 +315,19 @@ def run_gjp(args):
     proj_bytes = 4.0 * cg.n_views * cg.nu * cg.nv
     alg_bytes = {
         "forward_f32": 4.0 * foot.sum() + proj_bytes,
-        "forward_bf16": 2.0 * foot.sum() + proj_bytes,
+        k16: 2.0 * foot.sum() + proj_bytes,
         "adjoint_f32": 8.0 * foot.sum() + proj_bytes,    # read-modify-write of each touched voxel per view
     }
 
-    names = ["forward_f32", "forward_bf16", "adjoint_f32"]
+    names = ["forward_f32", k16, "adjoint_f32"]
 
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        gjp.forward(vol32, geom, vg.h, out=proj32)
+        gjp.forward(vol32, geom, vg.h, out=proj32, path=args.forward_path)
         if ev is not None:
             ev[1].record(stream)
-        gjp.forward(vol16, geom, vg.h, out=proj16)
+        gjp.forward(vol16, geom, vg.h, out=proj16, path=args.forward_path)
         if ev is not None:
             ev[2].record(stream)
         gjp.adjoint(proj32, geom, vg.n, vg.h, out=back)
@@ -362,10 +367,11 @@ def run_gjp(args):
         kernels[n] = {"ms": round(ms, 4), "gsamples_s": round(samples_per_kernel / (ms * 1e-3) / 1e9, 2),
                       "algorithmic_gb": round(alg_bytes[n] / 1e9, 4), "achieved_gbs": round(gbs, 1),
                       "frac_of_" + peak_kind + "_hbm": round(gbs / hbm, 4),
-                      "paper_logical_gbs": round(samples_per_kernel * (8 if "bf16" in n else 16)
+                      "paper_logical_gbs": round(samples_per_kernel * (8 if "16" in n and "f32" not in n else 16)
                                                  / (ms * 1e-3) / 1e9, 1)}
     dominant = max(names, key=lambda n: per_kernel_ms[n])
     kmap = {"forward_f32": "gjp_forward_kernel<float", "forward_bf16": "gjp_forward_kernel<__nv_bfloat16",
+            "forward_f16": "gjp_forward_tld4_kernel<__half",
             "adjoint_f32": "gjp_adjoint_combine_kernel<int"}
     traffic = dram_traffic(kmap[dominant])
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": kernels[dominant]["achieved_gbs"],
@@ -385,6 +391,7 @@ def run_gjp(args):
         else "synthetic (Shepp-Logan-shaped phantom, project-owned ellipsoids)",
         "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg.n_views,
                    "launch": {"tile_u": geom.launch[0], "view_group": geom.launch[1]},
+                   "forward_path": args.forward_path,
                    "step": "forward f32 + forward bf16 + adjoint f32", "samples_per_kernel": samples_per_kernel,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
         "kernels": kernels, "roofline": roofline, "clocks": clocks,
