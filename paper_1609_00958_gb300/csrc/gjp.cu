@@ -251,8 +251,8 @@ struct SlabShared {
 template <typename T, typename Index, int kBoxC>
 __global__ void __launch_bounds__(kSlabThreads, GJP_SLAB_MIN_BLOCKS) gjp_forward_slab_kernel(
     const T *__restrict__ vol, VolParams V, const ViewParams *__restrict__ views, int nu, int nv, int n_tv,
-    const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y, int box_r,
-    float *__restrict__ proj)
+    int n_views, int view_group, const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y,
+    int box_r, float *__restrict__ proj)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int kAlign = 16 / (int)sizeof(T);               // TMA x coordinate granularity
@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(kSlabThreads, GJP_SLAB_MIN_BLOCKS) gjp_forward
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp == kSlabWarps;
-    const int tile = blockIdx.x, view = blockIdx.y;
+    int tile, view;
+    block_tile_view(n_views, view_group, tile, view);
     const int v_base = (tile % n_tv) * 32, u_base = (tile / n_tv) * kSlabWarps;
     const int iv = v_base + lane, iu = u_base + warp;
     const bool have_ray = !producer && iv < nv && iu < nu;
@@ -803,8 +804,8 @@ struct AdjShared {
 template <typename Index, int kBoxC>
 __global__ void __launch_bounds__(kSlabWarps * 32, 3) gjp_adjoint_slab_kernel(
     const float *__restrict__ proj, VolParams V, const ViewParams *__restrict__ views, int nu, int nv, int n_tv,
-    const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y, int box_r,
-    float *__restrict__ vol)
+    int n_views, int view_group, const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y,
+    int box_r, float *__restrict__ vol)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int stage_elems = kPlanes * box_r * kBoxC;
@@ -814,7 +815,8 @@ __global__ void __launch_bounds__(kSlabWarps * 32, 3) gjp_adjoint_slab_kernel(
     const int stage_stride = stage_bytes / 4;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x, view = blockIdx.y;
+    int tile, view;
+    block_tile_view(n_views, view_group, tile, view);
     const int v_base = (tile % n_tv) * 32, u_base = (tile / n_tv) * kSlabWarps;
     const int iv = v_base + lane, iu = u_base + warp;
     const bool have_ray = iv < nv && iu < nu;
@@ -1182,7 +1184,8 @@ cudaError_t launch_slab(const T *vol, const VolParams &V, const ViewParams *tabl
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, kSlabThreads, smem, s>>>(vol, V, table, g.nu, g.nv, n_tv, mx, my, rows, proj);
+    kern<<<grid, kSlabThreads, smem, s>>>(vol, V, table, g.nu, g.nv, n_tv, g.n_views, g.view_group, mx, my, rows,
+                                          proj);
     return cudaGetLastError();
 }
 
@@ -1319,7 +1322,8 @@ cudaError_t launch_adjoint_slab(const float *proj, const VolParams &V, const Vie
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, kSlabWarps * 32, smem, s>>>(proj, V, table, g.nu, g.nv, n_tv, mx, my, rows, vol);
+    kern<<<grid, kSlabWarps * 32, smem, s>>>(proj, V, table, g.nu, g.nv, n_tv, g.n_views, g.view_group, mx, my,
+                                             rows, vol);
     return cudaGetLastError();
 }
 
