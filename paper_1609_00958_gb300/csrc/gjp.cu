@@ -647,24 +647,43 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_kernel(
 // One plane of the warp-combined adjoint (see above).  CHECKED tests each
 // tap against the grid (zero border) and, with CLIP, the plane against the
 // ray's clipped support; unchecked planes are interior for every lane.
-template <typename Index, bool SPL, bool CHECKED, bool CLIP>
+template <typename Index, bool SPL, bool CHECKED, bool CLIP, bool RUNS>
 __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, unsigned long long &pa,
                                               unsigned long long &pb, Index &plane, Index sa, unsigned na,
                                               unsigned nb, float *__restrict__ vol)
 {
     const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;
     const int ia = floor_of(pa), ib = floor_of(pb);
     const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
     const float yi = (!CLIP || (i >= R.s_lo && i <= R.s_hi)) ? yw : 0.0f;
     const float g1 = yi * db;                      // to voxel ib + 1
     const float g0 = __fmaf_rn(-yi, db, yi);       // yi (1 - db), to voxel ib
-    // the previous lane's upper tap joins this lane's lower tap when they
-    // are the same voxel (lane 0 receives its own values: never taken)
     const int ib_up = __shfl_up_sync(full, ib, 1);
     const float g1_up = __shfl_up_sync(full, g1, 1);
     const int ib_dn = __shfl_down_sync(full, ib, 1);
-    const float x0 = ib_up + 1 == ib ? g0 + g1_up : g0;
-    const float x1 = ib_dn == ib + 1 ? 0.0f : g1;    // kept when the next lane does not take it
+    float x0, x1;
+    if (RUNS) {
+        // At most two neighbouring lanes share a voxel (checked once per
+        // warp).  A run is one lane or two lanes on one voxel; its first lane
+        // adds the run's lower taps plus, when the previous run's voxel is
+        // the one just below, that run's upper taps; a run's last lane adds
+        // the run's upper taps itself only when no next run starts on that
+        // voxel.  Every voxel then has one writer.
+        const int dn = lane < 31 ? ib_dn - ib : 2;   // last lane: no next run
+        const int up = lane > 0 ? ib - ib_up : 2;    // first lane: no previous run
+        const float g0_dn = __shfl_down_sync(full, g0, 1);
+        const float e1 = up == 0 ? g1 + g1_up : g1;  // the run's upper taps, at its last lane
+        const float e1_up = __shfl_up_sync(full, e1, 1);
+        const float s0 = dn == 0 ? g0 + g0_dn : g0;  // the run's lower taps, at its first lane
+        x0 = up == 0 ? 0.0f : (up == 1 ? s0 + e1_up : s0);
+        x1 = (dn == 0 || dn == 1) ? 0.0f : e1;
+    } else {
+        // the previous lane's upper tap joins this lane's lower tap when they
+        // are the same voxel (lane 0 receives its own values: never taken)
+        x0 = ib_up + 1 == ib ? g0 + g1_up : g0;
+        x1 = ib_dn == ib + 1 ? 0.0f : g1;            // kept when the next lane does not take it
+    }
     float *p = vol + (plane + (Index)ia * sa + (Index)ib);
     const float wa0 = 1.0f - da;
     if (CHECKED) {
@@ -746,15 +765,42 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     // run without checks; the planes before and after check each tap.
     const int F0 = __reduce_max_sync(full, R.j_lo), F1 = __reduce_min_sync(full, R.j_hi);
     const int c_end = F0 <= F1 ? min(F0, I1 + 1) : I1 + 1;
+    // Run form when no three neighbouring lanes can share a voxel: lanes two
+    // apart differ by at least one voxel, with one sign, on the first and the
+    // last plane (the difference is affine in the plane index, so it then
+    // holds in between).
+    bool runs_ok = true;
+    {
+        const long long one = 1LL << 32;
+        long long d[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const long long p = pos_at(R.Pb, R.Gb, e ? I1 : I0, R.ic);
+            d[e] = __shfl_down_sync(full, p, 2) - p;
+        }
+        if (lane < 30 && !((d[0] >= one && d[1] >= one) || (d[0] <= -one && d[1] <= -one))) runs_ok = false;
+        runs_ok = __all_sync(full, runs_ok);
+    }
     int i = I0;
+    if (runs_ok) {
+        for (; i < c_end; ++i)
+            combine_plane<Index, SPL, true, CLIP, true>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+        if (F0 <= F1) {
+            for (; i <= min(F1, I1); ++i)
+                combine_plane<Index, SPL, false, false, true>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+        }
+        for (; i <= I1; ++i)
+            combine_plane<Index, SPL, true, CLIP, true>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+        return;
+    }
     for (; i < c_end; ++i)
-        combine_plane<Index, SPL, true, CLIP>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+        combine_plane<Index, SPL, true, CLIP, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
     if (F0 <= F1) {
         for (; i <= min(F1, I1); ++i)
-            combine_plane<Index, SPL, false, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+            combine_plane<Index, SPL, false, false, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
     }
     for (; i <= I1; ++i)
-        combine_plane<Index, SPL, true, CLIP>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+        combine_plane<Index, SPL, true, CLIP, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
 }
 
 // ---------------------------------------------------------------------------
