@@ -663,6 +663,7 @@ __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, uns
     const float g1_up = __shfl_up_sync(full, g1, 1);
     const int ib_dn = __shfl_down_sync(full, ib, 1);
     float x0, x1;
+    bool w0, w1;                                     // this lane adds to voxel ib / ib + 1
     if (RUNS) {
         // At most two neighbouring lanes share a voxel (checked once per
         // warp).  A run is one lane or two lanes on one voxel; its first lane
@@ -676,33 +677,37 @@ __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, uns
         const float e1 = up == 0 ? g1 + g1_up : g1;  // the run's upper taps, at its last lane
         const float e1_up = __shfl_up_sync(full, e1, 1);
         const float s0 = dn == 0 ? g0 + g0_dn : g0;  // the run's lower taps, at its first lane
-        x0 = up == 0 ? 0.0f : (up == 1 ? s0 + e1_up : s0);
-        x1 = (dn == 0 || dn == 1) ? 0.0f : e1;
+        x0 = up == 1 ? s0 + e1_up : s0;
+        x1 = e1;
+        w0 = up != 0;                                // first lane of its run
+        w1 = (unsigned)dn > 1u;                      // last lane, and no next run on voxel ib + 1
     } else {
         // the previous lane's upper tap joins this lane's lower tap when they
         // are the same voxel (lane 0 receives its own values: never taken)
         x0 = ib_up + 1 == ib ? g0 + g1_up : g0;
-        x1 = ib_dn == ib + 1 ? 0.0f : g1;            // kept when the next lane does not take it
+        x1 = g1;
+        w0 = x0 != 0.0f;
+        w1 = ib_dn != ib + 1 && g1 != 0.0f;          // kept when the next lane does not take it
     }
     float *p = vol + (plane + (Index)ia * sa + (Index)ib);
     const float wa0 = 1.0f - da;
     if (CHECKED) {
         const bool r0 = (unsigned)ia < na, r1 = (unsigned)(ia + 1) < na;   // zero border
         const bool z0 = (unsigned)ib < nb, z1 = (unsigned)(ib + 1) < nb;
-        if (z0 && x0 != 0.0f) {
+        if (z0 && w0) {
             if (r0) atomicAdd(p, wa0 * x0);
             if (r1) atomicAdd(p + sa, da * x0);
         }
-        if (z1 && x1 != 0.0f) {
+        if (z1 && w1) {
             if (r0) atomicAdd(p + 1, wa0 * x1);
             if (r1) atomicAdd(p + sa + 1, da * x1);
         }
     } else {
-        if (x0 != 0.0f) {
+        if (w0) {
             atomicAdd(p, wa0 * x0);
             atomicAdd(p + sa, da * x0);
         }
-        if (x1 != 0.0f) {
+        if (w1) {
             atomicAdd(p + 1, wa0 * x1);
             atomicAdd(p + sa + 1, da * x1);
         }
