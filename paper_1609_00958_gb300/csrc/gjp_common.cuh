@@ -60,7 +60,10 @@ struct VolParams {
 #endif
 constexpr int kTileV = 32;          // lanes of a warp along v (contiguous z)
 constexpr int kTileU = GJP_TILE_U;  // default warps of a block along u
-constexpr int kMaxTileU = 8;        // largest block: 8 warps
+#ifndef GJP_MAX_TILE_U
+#define GJP_MAX_TILE_U 8
+#endif
+constexpr int kMaxTileU = GJP_MAX_TILE_U;   // largest block: 8 warps
 constexpr int kMaxThreads = kTileV * kMaxTileU;
 constexpr int kBatch = GJP_BATCH;   // interior planes per batch
 // register budget of the one-thread-per-ray kernels: the same per-thread

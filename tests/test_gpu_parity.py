@@ -175,7 +175,7 @@ def test_adjoint_slab_equals_gather_full_size(gjp):
 
 
 @pytest.mark.parametrize("case", ["random", "random_steep", "coarse_detector", "unaligned_rows", "dense_detector",
-                                  "ragged"])
+                                  "rows_along_minus_z", "ragged"])
 @pytest.mark.parametrize("launch", [(4, 1), (8, 3), (1, 2)])
 def test_adjoint_combine_matches_oracle(gjp, case, launch):
     """The warp-combined adjoint against the oracle's transpose on the cases
@@ -197,6 +197,12 @@ def test_adjoint_combine_matches_oracle(gjp, case, launch):
     elif case == "dense_detector":
         vg = VolumeGeometry.centred((30, 30, 24))
         cg = synth.circular(4, 33, 70, 90.0, 180.0, 0.55)
+    elif case == "rows_along_minus_z":
+        # detector rows run along -z: a warp's z indices decrease lane by lane
+        vg = VolumeGeometry.centred((40, 36, 32))
+        cg = synth.cone_angle_geometry(40, 38, 5, 12.0)
+        cg.det_origin = cg.det_origin + (cg.nv - 1) * cg.det_v
+        cg.det_v = -cg.det_v
     else:
         vg = VolumeGeometry.centred((33, 35, 44))
         cg = synth.circular(3, 37, 45, 120.0, 240.0, 1.6, angles=[0.3, 1.9, 4.0])
