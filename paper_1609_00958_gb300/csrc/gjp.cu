@@ -128,9 +128,12 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocksMax) gjp_forward_kernel
     block_tile_view(n_views, view_group, tile, view);
     const int iv = (tile % n_tv) * kTileV + threadIdx.x;
     const int iu = (tile / n_tv) * (int)blockDim.y + threadIdx.y;
+    extern __shared__ uint4 gjp_fwd_rows[];            // 32 row-table entries (uint2) per warp
     const unsigned act = __ballot_sync(0xffffffffu, iv < nv && iu < nu);
     if (iv >= nv || iu >= nu) return;
-    proj[((size_t)view * nv + iv) * nu + iu] = forward_ray<T, Index, SPL>(vol, V, views + view, nu, nv, iu, iv, act);
+    proj[((size_t)view * nv + iv) * nu + iu] =
+        forward_ray<T, Index, SPL>(vol, V, views + view, nu, nv, iu, iv, act,
+                                   reinterpret_cast<uint2 *>(gjp_fwd_rows + 16 * threadIdx.y));
 }
 
 // ---------------------------------------------------------------------------
@@ -1301,9 +1304,12 @@ cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *ta
     const dim3 block(kTileV, g.tile_u);
     const bool spl = g.weight == GJP_WEIGHT_SPL;
     const int nvw = g.n_views, vgp = g.view_group;
+    const size_t rows = (size_t)g.tile_u * 32 * sizeof(uint2);   // row tables (32-bit offsets only)
     if (i32) {
-        if (spl) gjp_forward_kernel<T, int, true><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
-        else gjp_forward_kernel<T, int, false><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
+        if (spl)
+            gjp_forward_kernel<T, int, true><<<grid, block, rows, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
+        else
+            gjp_forward_kernel<T, int, false><<<grid, block, rows, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
     } else {
         if (spl)
             gjp_forward_kernel<T, long long, true><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);

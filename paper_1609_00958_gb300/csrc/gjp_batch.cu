@@ -49,7 +49,8 @@ struct BatchProblem {
 
 // One work item: tile `tile` of view `view` (item numbering of block_tile_view).
 template <typename T, typename Index, bool SPL>
-__device__ __forceinline__ void batch_item(const BatchProblem &P, int tile, int view, int warp, int lane)
+__device__ __forceinline__ void batch_item(const BatchProblem &P, int tile, int view, int warp, int lane,
+                                           uint2 *rows)
 {
     const int rows_per_tile = kBatchWarps / P.tile_u;          // 32-row groups per tile
     const int tu = tile / P.n_tr, tr = tile % P.n_tr;
@@ -59,24 +60,26 @@ __device__ __forceinline__ void batch_item(const BatchProblem &P, int tile, int 
     const unsigned act = __ballot_sync(0xffffffffu, active);
     if (!active) return;
     const float val = forward_ray<T, Index, SPL>(static_cast<const T *>(P.vol), P.V, P.table + view, P.nu, P.nv,
-                                                 iu, iv, act);
+                                                 iu, iv, act, rows);
     P.proj[((size_t)view * P.nv + iv) * P.nu + iu] = val;
 }
 
 // The kernel is instantiated with only the variants its problems need
 // (64-bit offsets, w_spl weights), which keeps its code small.
 template <typename T, typename Index, bool ANY_SPL>
-__device__ __forceinline__ void batch_item_w(const BatchProblem &P, int tile, int view, int warp, int lane)
+__device__ __forceinline__ void batch_item_w(const BatchProblem &P, int tile, int view, int warp, int lane,
+                                             uint2 *rows)
 {
-    if (ANY_SPL && (P.kind & 8)) batch_item<T, Index, ANY_SPL>(P, tile, view, warp, lane);
-    else batch_item<T, Index, false>(P, tile, view, warp, lane);
+    if (ANY_SPL && (P.kind & 8)) batch_item<T, Index, ANY_SPL>(P, tile, view, warp, lane, rows);
+    else batch_item<T, Index, false>(P, tile, view, warp, lane, rows);
 }
 
 template <typename T, bool ANY_I64, bool ANY_SPL>
-__device__ __forceinline__ void batch_item_i(const BatchProblem &P, int tile, int view, int warp, int lane)
+__device__ __forceinline__ void batch_item_i(const BatchProblem &P, int tile, int view, int warp, int lane,
+                                             uint2 *rows)
 {
-    if (!ANY_I64 || (P.kind & 4)) batch_item_w<T, int, ANY_SPL>(P, tile, view, warp, lane);
-    else batch_item_w<T, long long, ANY_SPL>(P, tile, view, warp, lane);
+    if (!ANY_I64 || (P.kind & 4)) batch_item_w<T, int, ANY_SPL>(P, tile, view, warp, lane, rows);
+    else batch_item_w<T, long long, ANY_SPL>(P, tile, view, warp, lane, rows);
 }
 
 // begins[p] = first queue index of problem p, begins[n_probs] = total.
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(kBatchThreads, 8) gjp_batch_forward_kernel(
 {
     __shared__ long long s_begin[kBatchMaxProblems + 1];
     __shared__ unsigned long long s_item;
+    __shared__ __align__(16) uint2 s_rows[kBatchWarps][32];   // row tables, one per warp
     for (int k = threadIdx.x; k <= n_probs; k += blockDim.x) s_begin[k] = begins[k];
     __syncthreads();
     const long long total = s_begin[n_probs];
@@ -116,9 +120,9 @@ __global__ void __launch_bounds__(kBatchThreads, 8) gjp_batch_forward_kernel(
             const int gl = min(P.view_group, P.n_views - v0);
             const int view = v0 + r % gl, tile = r / gl;
             switch (P.kind & 3) {
-            case GJP_F32: batch_item_i<float, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
-            case GJP_BF16: batch_item_i<__nv_bfloat16, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
-            default: batch_item_i<__half, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
+            case GJP_F32: batch_item_i<float, ANY_I64, ANY_SPL>(P, tile, view, warp, lane, s_rows[warp]); break;
+            case GJP_BF16: batch_item_i<__nv_bfloat16, ANY_I64, ANY_SPL>(P, tile, view, warp, lane, s_rows[warp]); break;
+            default: batch_item_i<__half, ANY_I64, ANY_SPL>(P, tile, view, warp, lane, s_rows[warp]); break;
             }
         }
     }

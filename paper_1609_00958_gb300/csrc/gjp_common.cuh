@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -57,6 +58,11 @@ struct VolParams {
 #endif
 #ifndef GJP_VIEW_GROUP
 #define GJP_VIEW_GROUP 8   // default launch order: 8 views per detector tile
+#endif
+// Warps whose 32 rays share their first transverse row march from a shared
+// per-warp row table (1) or each lane steps its own row position (0).
+#ifndef GJP_ROWS
+#define GJP_ROWS 1
 #endif
 constexpr int kTileV = 32;          // lanes of a warp along v (contiguous z)
 constexpr int kTileU = GJP_TILE_U;  // default warps of a block along u
@@ -536,6 +542,127 @@ __device__ __forceinline__ float march_boundary(const T *__restrict__ vol, const
     return acc;
 }
 
+// One 16-plane block of the row-table march (below): entries e[0..15] give
+// each plane's row weight and row offset (read two at a time), pb steps
+// along z.  CHECKED loads only the taps of planes 0 <= d + t < cnt (this
+// lane's interior), the others contribute zero, and stops after `n` planes
+// (warp-uniform: no lane has an interior plane past them).
+template <typename T, bool SPL, bool CHECKED>
+__device__ __forceinline__ float rows_block(const T *__restrict__ vol, const uint2 *__restrict__ e,
+                                            unsigned long long &pb, unsigned long long gb, int sa, int d, int cnt,
+                                            int n)
+{
+    float blk = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (CHECKED && q * kBatch >= n) break;
+        float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
+        unsigned off[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; t += 2) {
+            const uint4 en = *reinterpret_cast<const uint4 *>(e + q * kBatch + t);
+            da[t] = __uint_as_float(en.x);
+            off[t] = en.y;
+            da[t + 1] = __uint_as_float(en.z);
+            off[t + 1] = en.w;
+        }
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+            db[t] = upper_weight<SPL>(frac_of(pb));
+            const T *p = vol + (int)(off[t] + (unsigned)floor_of(pb));
+            if (CHECKED) {
+                const bool in = (unsigned)(d + q * kBatch + t) < (unsigned)cnt;
+                v00[t] = in ? load_voxel(p) : 0.0f;
+                v01[t] = in ? load_voxel(p + 1) : 0.0f;
+                v10[t] = in ? load_voxel(p + sa) : 0.0f;
+                v11[t] = in ? load_voxel(p + sa + 1) : 0.0f;
+            } else {
+                v00[t] = load_voxel(p);
+                v01[t] = load_voxel(p + 1);
+                v10[t] = load_voxel(p + sa);
+                v11[t] = load_voxel(p + sa + 1);
+            }
+            pb += gb;
+        }
+        float bsum = 0.0f;
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+            const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
+            const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
+            bsum += __fmaf_rn(da[t], e1 - e0, e0);
+        }
+        blk += bsum;
+    }
+    return blk;
+}
+
+// Interior planes of a warp whose 32 rays share their first transverse row:
+// the same driving axis (x or y, so the second transverse axis is z), the
+// same Pa and the same Ga -- every ray of a detector column when the orbit
+// turns about z.  The row index ia, its weight and the plane's offset are
+// then the same on every lane, so the warp computes each plane's row once:
+// lane k fills the entry of the k-th of the next 32 planes, and every lane
+// reads the entries with broadcast shared-memory loads instead of stepping,
+// splitting and scaling its own copy of the row position.  The lanes march
+// the warp's planes together; a 16-plane block inside every lane's interior
+// runs without checks, other blocks load only the taps of lanes whose
+// interior holds the plane (their boundary planes are summed elsewhere).
+// `rows` is this warp's 32-entry table, 16-byte aligned: (row weight bits,
+// row offset) per plane.
+template <typename T, bool SPL>
+__device__ __forceinline__ float march_interior_rows(const T *__restrict__ vol, const Ray &R, bool rev,
+                                                     uint2 *__restrict__ rows, int lane)
+{
+    const unsigned full = 0xffffffffu;
+    const bool has = R.j_lo <= R.j_hi;
+    const int I0 = __reduce_min_sync(full, has ? R.j_lo : INT_MAX);
+    const int I1 = __reduce_max_sync(full, has ? R.j_hi : INT_MIN);
+    if (I0 > I1) return 0.0f;                         // no lane has an interior plane (warp-uniform)
+    const int L = I1 - I0 + 1;                        // step k visits plane i0 + dir k
+    const int i0 = rev ? I1 : I0, dir = rev ? -1 : 1;
+    const int cnt = has ? R.j_hi - R.j_lo + 1 : 0;   // this lane: steps k_lo .. k_lo + cnt - 1
+    const int k_lo = rev ? I1 - R.j_hi : R.j_lo - I0;
+    // steps at which every lane is interior (none when a lane has no interior)
+    const int K0 = __reduce_max_sync(full, has ? k_lo : INT_MAX);
+    const int K1 = __reduce_min_sync(full, has ? k_lo + cnt - 1 : INT_MIN);
+
+    const int sa = R.sa;
+    unsigned long long pb = (unsigned long long)pos_at(R.Pb, R.Gb, i0, R.ic);
+    const unsigned long long gb = rev ? 0ull - (unsigned long long)R.Gb : (unsigned long long)R.Gb;
+    // this lane's table plane in window w: i0 + dir (32 w + lane); offsets in
+    // unsigned arithmetic (planes past the warp's range are filled, never read)
+    unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, i0 + dir * lane, R.ic);
+    const unsigned long long ga32 = (rev ? 0ull - (unsigned long long)R.Ga : (unsigned long long)R.Ga) << 5;
+    unsigned row = (unsigned)(i0 + dir * lane) * (unsigned)R.sm;
+    const unsigned sm32 = (unsigned)(dir * 32) * (unsigned)R.sm;
+
+    float acc = 0.0f;
+    for (int w = 0; w < L; w += 32) {
+        __syncwarp();                                 // every lane has read the last window
+        rows[lane] = make_uint2(__float_as_uint(upper_weight<SPL>(frac_of(pa))),
+                                row + (unsigned)floor_of(pa) * (unsigned)sa);
+        pa += ga32;
+        row += sm32;
+        __syncwarp();
+        const int nw = min(32, L - w);
+        for (int kb = 0; kb < nw; kb += 16) {
+            const int k = w + kb;
+            if (k >= K0 && k + 15 <= K1)              // warp-uniform
+                acc += rows_block<T, SPL, false>(vol, rows + kb, pb, gb, sa, 0, 0, 16);
+            else
+                acc += rows_block<T, SPL, true>(vol, rows + kb, pb, gb, sa, k - k_lo, cnt, L - k);
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ int lane_id()
+{
+    int l;
+    asm("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+
 // GJP line integral of the ray through detector pixel (iu, iv) of the view
 // whose table entry is *view (Algorithm 1).  Called by every lane of the
 // warp set in `act` (the lanes that hold a ray; they share the warp-level
@@ -543,7 +670,7 @@ __device__ __forceinline__ float march_boundary(const T *__restrict__ vol, const
 template <typename T, typename Index, bool SPL>
 __device__ __forceinline__ float forward_ray(const T *__restrict__ vol, const VolParams &V,
                                              const ViewParams *__restrict__ view, int nu, int nv, int iu, int iv,
-                                             unsigned act)
+                                             unsigned act, uint2 *__restrict__ rows = nullptr)
 {
     ViewParams vp;
     load_view(view, 0, vp);
@@ -562,6 +689,15 @@ __device__ __forceinline__ float forward_ray(const T *__restrict__ vol, const Vo
     // the few boundary planes first: afterwards only the interior march's
     // state stays live, which keeps the unrolled loop within the register budget
     const float bsum = march_boundary<T, Index, SPL>(vol, R);
+    if constexpr (std::is_same<Index, int>::value) {
+        // a full warp with one common row: the shared row table
+        if (GJP_ROWS && rows != nullptr && act == 0xffffffffu) {
+            const int m0 = __shfl_sync(act, R.m, 0);
+            const long long Pa0 = __shfl_sync(act, R.Pa, 0), Ga0 = __shfl_sync(act, R.Ga, 0);
+            if (__all_sync(act, R.m == m0 && R.Pa == Pa0 && R.Ga == Ga0) && m0 != 2)
+                return (march_interior_rows<T, SPL>(vol, R, rev, rows, lane_id()) + bsum) * R.step;
+        }
+    }
     const float acc = (R.m != 2) ? march_interior<T, Index, true, SPL>(vol, R, rev)
                                  : march_interior<T, Index, false, SPL>(vol, R, rev);
     return (acc + bsum) * R.step;
