@@ -104,7 +104,7 @@ gjp_status gjp_geometry_set_weight(gjp_geometry *g, gjp_weight w);
  * is that knob, plus the order in which blocks are issued.
  *   tile_u     : detector columns per block, 1, 2, 4 (default) or 8; a
  *                block is tile_u warps of 32 detector rows.
- *   view_group : 1 .. 64 (default 8).  Blocks are issued so that
+ *   view_group : 1 .. 64 (default 16).  Blocks are issued so that
  *                view_group consecutive views are processed tile by tile
  *                together (their rays cross nearly the same voxels, which
  *                then come from the L2 cache); 1 issues the views one

@@ -53,7 +53,7 @@ class Geometry:
             raise GjpError(st, "gjp_geometry_set_weight")
         self.weight = weight
 
-    def set_launch(self, tile_u: int = 4, view_group: int = 8):
+    def set_launch(self, tile_u: int = 4, view_group: int = 16):
         """Launch shape of the one-thread-per-ray kernels: ``tile_u`` detector
         columns per block (1, 2, 4 or 8) and ``view_group`` views issued tile
         by tile together.  Changes speed only, never a result."""

@@ -128,12 +128,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocksMax) gjp_forward_kernel
     block_tile_view(n_views, view_group, tile, view);
     const int iv = (tile % n_tv) * kTileV + threadIdx.x;
     const int iu = (tile / n_tv) * (int)blockDim.y + threadIdx.y;
-    extern __shared__ uint4 gjp_fwd_rows[];            // 32 row-table entries (uint2) per warp
     const unsigned act = __ballot_sync(0xffffffffu, iv < nv && iu < nu);
     if (iv >= nv || iu >= nu) return;
     proj[((size_t)view * nv + iv) * nu + iu] =
-        forward_ray<T, Index, SPL>(vol, V, views + view, nu, nv, iu, iv, act,
-                                   reinterpret_cast<uint2 *>(gjp_fwd_rows + 16 * threadIdx.y));
+        forward_ray<T, Index, SPL>(vol, V, views + view, nu, nv, iu, iv, act, (int)threadIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -647,26 +645,32 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_kernel(
 // does not depend on how the rays are spaced.  This halves the reductions
 // of the tap-by-tap scatter.  Warps without a common row scatter tap by tap.
 
-// One plane of the warp-combined adjoint (see above).  CHECKED tests each
-// tap against the grid (zero border) and, with CLIP, the plane against the
-// ray's clipped support; unchecked planes are interior for every lane.
-template <typename Index, bool SPL, bool CHECKED, bool CLIP, bool RUNS>
-__device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, unsigned long long &pa,
-                                              unsigned long long &pb, Index &plane, Index sa, unsigned na,
-                                              unsigned nb, float *__restrict__ vol)
+// Reductions at p0 and p1 when w is set.  (The branch form measured faster
+// than reductions predicated in the instruction, which also made the
+// compiler emit more branches around them.)
+__device__ __forceinline__ void red_add2_if(bool w, float *p0, float v0, float *p1, float v1)
+{
+    if (w) {
+        atomicAdd(p0, v0);
+        atomicAdd(p1, v1);
+    }
+}
+
+__device__ __forceinline__ void red_add_if(bool w, float *p, float v)
+{
+    if (w) atomicAdd(p, v);
+}
+
+// What one lane adds to voxels ib (x0, when w0) and ib + 1 (x1, when w1) of
+// both rows, given its taps g0 (to ib) and g1 (to ib + 1); see above.
+template <bool RUNS>
+__device__ __forceinline__ void combine_lane(int ib, float g0, float g1, float &x0, float &x1, bool &w0, bool &w1)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x;
-    const int ia = floor_of(pa), ib = floor_of(pb);
-    const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
-    const float yi = (!CLIP || (i >= R.s_lo && i <= R.s_hi)) ? yw : 0.0f;
-    const float g1 = yi * db;                      // to voxel ib + 1
-    const float g0 = __fmaf_rn(-yi, db, yi);       // yi (1 - db), to voxel ib
     const int ib_up = __shfl_up_sync(full, ib, 1);
     const float g1_up = __shfl_up_sync(full, g1, 1);
     const int ib_dn = __shfl_down_sync(full, ib, 1);
-    float x0, x1;
-    bool w0, w1;                                     // this lane adds to voxel ib / ib + 1
     if (RUNS) {
         // At most two neighbouring lanes share a voxel (checked once per
         // warp).  A run is one lane or two lanes on one voxel; its first lane
@@ -692,32 +696,96 @@ __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, uns
         w0 = x0 != 0.0f;
         w1 = ib_dn != ib + 1 && g1 != 0.0f;          // kept when the next lane does not take it
     }
+}
+
+// One plane of the warp-combined adjoint (see above).  CHECKED tests each
+// tap against the grid (zero border) and, with CLIP, the plane against the
+// ray's clipped support; unchecked planes are interior for every lane.
+template <typename Index, bool SPL, bool CHECKED, bool CLIP, bool RUNS>
+__device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, unsigned long long &pa,
+                                              unsigned long long &pb, Index &plane, Index sa, unsigned na,
+                                              unsigned nb, float *__restrict__ vol)
+{
+    const int ia = floor_of(pa), ib = floor_of(pb);
+    const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
+    const float yi = (!CLIP || (i >= R.s_lo && i <= R.s_hi)) ? yw : 0.0f;
+    const float g1 = yi * db;                      // to voxel ib + 1
+    const float g0 = __fmaf_rn(-yi, db, yi);       // yi (1 - db), to voxel ib
+    float x0, x1;
+    bool w0, w1;                                     // this lane adds to voxel ib / ib + 1
+    combine_lane<RUNS>(ib, g0, g1, x0, x1, w0, w1);
     float *p = vol + (plane + (Index)ia * sa + (Index)ib);
     const float wa0 = 1.0f - da;
     if (CHECKED) {
         const bool r0 = (unsigned)ia < na, r1 = (unsigned)(ia + 1) < na;   // zero border
         const bool z0 = (unsigned)ib < nb, z1 = (unsigned)(ib + 1) < nb;
-        if (z0 && w0) {
-            if (r0) atomicAdd(p, wa0 * x0);
-            if (r1) atomicAdd(p + sa, da * x0);
-        }
-        if (z1 && w1) {
-            if (r0) atomicAdd(p + 1, wa0 * x1);
-            if (r1) atomicAdd(p + sa + 1, da * x1);
-        }
+        red_add_if(z0 && w0 && r0, p, wa0 * x0);
+        red_add_if(z0 && w0 && r1, p + sa, da * x0);
+        red_add_if(z1 && w1 && r0, p + 1, wa0 * x1);
+        red_add_if(z1 && w1 && r1, p + sa + 1, da * x1);
     } else {
-        if (w0) {
-            atomicAdd(p, wa0 * x0);
-            atomicAdd(p + sa, da * x0);
-        }
-        if (w1) {
-            atomicAdd(p + 1, wa0 * x1);
-            atomicAdd(p + sa + 1, da * x1);
-        }
+        red_add2_if(w0, p, wa0 * x0, p + sa, da * x0);
+        red_add2_if(w1, p + 1, wa0 * x1, p + sa + 1, da * x1);
     }
     pa += (unsigned long long)R.Ga;
     pb += (unsigned long long)R.Gb;
     plane += (Index)R.sm;
+}
+
+// One unchecked plane whose row weight and row offset come from the warp's
+// row table (entry weight bits, offset).
+template <bool SPL, bool RUNS>
+__device__ __forceinline__ void combine_row_plane(float yw, unsigned wbits, unsigned off, unsigned long long &pb,
+                                                  unsigned long long gb, int sa, float *__restrict__ vol)
+{
+    const int ib = floor_of(pb);
+    const float db = upper_weight<SPL>(frac_of(pb));
+    const float g1 = yw * db;
+    const float g0 = __fmaf_rn(-yw, db, yw);
+    float x0, x1;
+    bool w0, w1;
+    combine_lane<RUNS>(ib, g0, g1, x0, x1, w0, w1);
+    float *p = vol + (int)(off + (unsigned)ib);
+    const float da = __uint_as_float(wbits), wa0 = 1.0f - da;
+    red_add2_if(w0, p, wa0 * x0, p + sa, da * x0);
+    red_add2_if(w1, p + 1, wa0 * x1, p + sa + 1, da * x1);
+    pb += gb;
+}
+
+// Unchecked planes i_lo .. i_hi of a warp on one row (32-bit offsets): the
+// row position is stepped once per plane for the whole warp, as in the
+// forward's row-table march -- lane k fills the entry of the k-th of the
+// next 32 planes, and every lane reads them from shared memory.
+template <bool SPL, bool RUNS>
+__device__ __forceinline__ void combine_rows(const Ray &R, int i_lo, int i_hi, float yw, unsigned long long &pb,
+                                             uint2 *__restrict__ rows, float *__restrict__ vol)
+{
+    const int lane = threadIdx.x;
+    const int sa = (int)R.sa;
+    const unsigned long long gb = (unsigned long long)R.Gb;
+    unsigned long long pa = (unsigned long long)pos_at(R.Pa, R.Ga, i_lo + lane, R.ic);
+    const unsigned long long ga32 = (unsigned long long)R.Ga << 5;
+    unsigned row = (unsigned)(i_lo + lane) * (unsigned)R.sm;
+    const unsigned sm32 = 32u * (unsigned)R.sm;
+    for (int w = i_lo; w <= i_hi; w += 32) {
+        __syncwarp();                                 // every lane has read the last window
+        rows[lane] = make_uint2(__float_as_uint(upper_weight<SPL>(frac_of(pa))),
+                                row + (unsigned)floor_of(pa) * (unsigned)sa);
+        pa += ga32;
+        row += sm32;
+        __syncwarp();
+        const int n = min(32, i_hi - w + 1);
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+            const uint4 e = *reinterpret_cast<const uint4 *>(rows + j);
+            combine_row_plane<SPL, RUNS>(yw, e.x, e.y, pb, gb, sa, vol);
+            combine_row_plane<SPL, RUNS>(yw, e.z, e.w, pb, gb, sa, vol);
+        }
+        if (j < n) {
+            const uint2 e = rows[j];
+            combine_row_plane<SPL, RUNS>(yw, e.x, e.y, pb, gb, sa, vol);
+        }
+    }
 }
 
 template <typename Index, bool SPL, bool CLIP>
@@ -747,6 +815,9 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     const int m0 = __shfl_sync(full, R.m, 0);
     const long long Pa0 = __shfl_sync(full, R.Pa, 0), Ga0 = __shfl_sync(full, R.Ga, 0);
     const bool uniform = __all_sync(full, R.m == m0 && R.Pa == Pa0 && R.Ga == Ga0) && m0 != 2;
+    // unchecked planes step the shared row once per warp (32-bit offsets)
+    constexpr bool USE_ROWS = GJP_ROWS && std::is_same<Index, int>::value;
+    uint2 *rows = row_table(threadIdx.y);
     if (!uniform) {
         if (ys != 0.0f) scatter_ray<Index, SPL>(R, ys, vol);
         return;
@@ -794,7 +865,14 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
         for (; i < c_end; ++i)
             combine_plane<Index, SPL, true, CLIP, true>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
         if (F0 <= F1) {
-            for (; i <= min(F1, I1); ++i)
+            const int hi = min(F1, I1);
+            if (USE_ROWS && i <= hi) {
+                combine_rows<SPL, true>(R, i, hi, yw, pb, rows, vol);
+                i = hi + 1;
+                pa = (unsigned long long)pos_at(R.Pa, R.Ga, i, R.ic);
+                plane = (Index)i * sm;
+            }
+            for (; i <= hi; ++i)
                 combine_plane<Index, SPL, false, false, true>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
         }
         for (; i <= I1; ++i)
@@ -804,7 +882,14 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     for (; i < c_end; ++i)
         combine_plane<Index, SPL, true, CLIP, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
     if (F0 <= F1) {
-        for (; i <= min(F1, I1); ++i)
+        const int hi = min(F1, I1);
+        if (USE_ROWS && i <= hi) {
+            combine_rows<SPL, false>(R, i, hi, yw, pb, rows, vol);
+            i = hi + 1;
+            pa = (unsigned long long)pos_at(R.Pa, R.Ga, i, R.ic);
+            plane = (Index)i * sm;
+        }
+        for (; i <= hi; ++i)
             combine_plane<Index, SPL, false, false, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
     }
     for (; i <= I1; ++i)
@@ -1095,6 +1180,29 @@ bool fits_int32(const int64_t n[3])
 }
 
 size_t elem_size(gjp_dtype t) { return t == GJP_F32 ? 4 : 2; }
+
+void fit_carveout(const void *func, int threads, size_t dyn_smem)
+{
+    int dev = 0, per_sm = 0, smem_sm = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, dyn_smem) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, func) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        per_sm < 1 || smem_sm < 1) {
+        cudaGetLastError();
+        return;
+    }
+    const size_t need = (size_t)per_sm * (fa.sharedSizeBytes + dyn_smem + (size_t)reserved);
+    const int pct = (int)std::min<size_t>(100, (need * 100 + (size_t)smem_sm - 1) / (size_t)smem_sm);
+    int after = 0;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&after, func, threads, dyn_smem) != cudaSuccess ||
+        after < per_sm)
+        cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, -1);
+    cudaGetLastError();
+}
 
 // cuTensorMapEncodeTiled, fetched once through the runtime (no link to libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -1718,8 +1826,10 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
         const dim3 block(kTileV, g->tile_u);
         const int nvw = g->n_views, vgp = g->view_group;
         const bool clip = V.fov_r2 > 0.0f;
+        const size_t rows = (size_t)g->tile_u * 32 * sizeof(uint2);   // row tables
 #define GJP_COMBINE_LAUNCH(I, S, C)                                                                                \
-    gjp_adjoint_combine_kernel<I, S, C><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw, vgp, d_volume)
+    gjp_adjoint_combine_kernel<I, S, C><<<grid, block, rows, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw, vgp,   \
+                                                                  d_volume)
         if (fits_int32(n)) {
             if (spl) { if (clip) GJP_COMBINE_LAUNCH(int, true, true); else GJP_COMBINE_LAUNCH(int, true, false); }
             else { if (clip) GJP_COMBINE_LAUNCH(int, false, true); else GJP_COMBINE_LAUNCH(int, false, false); }

@@ -27,6 +27,7 @@ namespace {
 
 constexpr int kBatchWarps = 4;                       // one block: 4 warps, 128 rays
 constexpr int kBatchThreads = kBatchWarps * 32;
+constexpr size_t kBatchRowBytes = kBatchWarps * 32 * sizeof(uint2);   // dynamic shared: row tables
 #ifndef GJP_BATCH_CHUNK
 #define GJP_BATCH_CHUNK 1
 #endif
@@ -34,7 +35,7 @@ constexpr int kBatchChunk = GJP_BATCH_CHUNK;         // items taken per queue fe
 constexpr int kBatchMaxProblems = 256;
 constexpr int kTuneViews = 24;                       // views timed per autotuner candidate
 
-struct BatchProblem {
+struct __align__(8) BatchProblem {
     const void *vol;
     float *proj;
     const ViewParams *table;
@@ -49,8 +50,7 @@ struct BatchProblem {
 
 // One work item: tile `tile` of view `view` (item numbering of block_tile_view).
 template <typename T, typename Index, bool SPL>
-__device__ __forceinline__ void batch_item(const BatchProblem &P, int tile, int view, int warp, int lane,
-                                           uint2 *rows)
+__device__ __forceinline__ void batch_item(const BatchProblem &P, int tile, int view, int warp, int lane)
 {
     const int rows_per_tile = kBatchWarps / P.tile_u;          // 32-row groups per tile
     const int tu = tile / P.n_tr, tr = tile % P.n_tr;
@@ -60,26 +60,24 @@ __device__ __forceinline__ void batch_item(const BatchProblem &P, int tile, int 
     const unsigned act = __ballot_sync(0xffffffffu, active);
     if (!active) return;
     const float val = forward_ray<T, Index, SPL>(static_cast<const T *>(P.vol), P.V, P.table + view, P.nu, P.nv,
-                                                 iu, iv, act, rows);
+                                                 iu, iv, act, warp);
     P.proj[((size_t)view * P.nv + iv) * P.nu + iu] = val;
 }
 
 // The kernel is instantiated with only the variants its problems need
 // (64-bit offsets, w_spl weights), which keeps its code small.
 template <typename T, typename Index, bool ANY_SPL>
-__device__ __forceinline__ void batch_item_w(const BatchProblem &P, int tile, int view, int warp, int lane,
-                                             uint2 *rows)
+__device__ __forceinline__ void batch_item_w(const BatchProblem &P, int tile, int view, int warp, int lane)
 {
-    if (ANY_SPL && (P.kind & 8)) batch_item<T, Index, ANY_SPL>(P, tile, view, warp, lane, rows);
-    else batch_item<T, Index, false>(P, tile, view, warp, lane, rows);
+    if (ANY_SPL && (P.kind & 8)) batch_item<T, Index, ANY_SPL>(P, tile, view, warp, lane);
+    else batch_item<T, Index, false>(P, tile, view, warp, lane);
 }
 
 template <typename T, bool ANY_I64, bool ANY_SPL>
-__device__ __forceinline__ void batch_item_i(const BatchProblem &P, int tile, int view, int warp, int lane,
-                                             uint2 *rows)
+__device__ __forceinline__ void batch_item_i(const BatchProblem &P, int tile, int view, int warp, int lane)
 {
-    if (!ANY_I64 || (P.kind & 4)) batch_item_w<T, int, ANY_SPL>(P, tile, view, warp, lane, rows);
-    else batch_item_w<T, long long, ANY_SPL>(P, tile, view, warp, lane, rows);
+    if (!ANY_I64 || (P.kind & 4)) batch_item_w<T, int, ANY_SPL>(P, tile, view, warp, lane);
+    else batch_item_w<T, long long, ANY_SPL>(P, tile, view, warp, lane);
 }
 
 // begins[p] = first queue index of problem p, begins[n_probs] = total.
@@ -88,42 +86,53 @@ __global__ void __launch_bounds__(kBatchThreads, 8) gjp_batch_forward_kernel(
     const BatchProblem *__restrict__ probs, const long long *__restrict__ begins, int n_probs,
     unsigned long long *__restrict__ counter, int chunk)
 {
+    // Everything the loop needs across an item lives in shared memory or
+    // kernel parameters, so the march keeps the whole register budget (as
+    // in the one-problem kernel) and the item's loads stay in flight.
     __shared__ long long s_begin[kBatchMaxProblems + 1];
-    __shared__ unsigned long long s_item;
-    __shared__ __align__(16) uint2 s_rows[kBatchWarps][32];   // row tables, one per warp
+    __shared__ long long s_it, s_end;                  // the block's item and the end of its fetched range
+    __shared__ BatchProblem s_prob;                    // the item's problem
     for (int k = threadIdx.x; k <= n_probs; k += blockDim.x) s_begin[k] = begins[k];
-    __syncthreads();
-    const long long total = s_begin[n_probs];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_it = s_end = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, (unsigned long long)chunk);
+        __syncthreads();                               // the last item's rays are done
+        if (threadIdx.x == 0) {
+            long long it = s_it + 1;
+            if (it >= s_end) {                         // range used up (or none yet): fetch
+                it = (long long)atomicAdd(counter, (unsigned long long)chunk);
+                s_end = it + chunk;
+            }
+            s_it = it;
+        }
         __syncthreads();
-        const long long first = (long long)s_item;
-        __syncthreads();                                       // s_item is rewritten next round
-        if (first >= total) break;
-        const long long last = first + chunk < total ? first + chunk : total;
-        for (long long it = first; it < last; ++it) {
-            int lo = 0, hi = n_probs - 1;                      // last problem with begin <= it
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_begin[mid] <= it) lo = mid;
-                else hi = mid - 1;
-            }
-            const BatchProblem P = probs[lo];
-            // item -> (tile, view): block_tile_view's numbering for one problem
-            const long long local = it - s_begin[lo];
-            const long long n_tiles = (long long)P.n_tu * P.n_tr;
-            const long long per = n_tiles * P.view_group;
-            const int grp = (int)(local / per);
-            const int r = (int)(local - (long long)grp * per);
-            const int v0 = grp * P.view_group;
-            const int gl = min(P.view_group, P.n_views - v0);
-            const int view = v0 + r % gl, tile = r / gl;
-            switch (P.kind & 3) {
-            case GJP_F32: batch_item_i<float, ANY_I64, ANY_SPL>(P, tile, view, warp, lane, s_rows[warp]); break;
-            case GJP_BF16: batch_item_i<__nv_bfloat16, ANY_I64, ANY_SPL>(P, tile, view, warp, lane, s_rows[warp]); break;
-            default: batch_item_i<__half, ANY_I64, ANY_SPL>(P, tile, view, warp, lane, s_rows[warp]); break;
-            }
+        const long long it = s_it;
+        if (it >= s_begin[n_probs]) break;             // queue exhausted (block-uniform)
+        int lo = 0, hi = n_probs - 1;                  // last problem with begin <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_begin[mid] <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        constexpr int kWords = (int)(sizeof(BatchProblem) / sizeof(long long));
+        if (threadIdx.x < kWords)
+            reinterpret_cast<long long *>(&s_prob)[threadIdx.x] =
+                reinterpret_cast<const long long *>(probs + lo)[threadIdx.x];
+        __syncthreads();
+        const BatchProblem &P = s_prob;
+        // item -> (tile, view): block_tile_view's numbering for one problem
+        const long long local = it - s_begin[lo];
+        const long long n_tiles = (long long)P.n_tu * P.n_tr;
+        const long long per = n_tiles * P.view_group;
+        const int grp = (int)(local / per);
+        const int r = (int)(local - (long long)grp * per);
+        const int v0 = grp * P.view_group;
+        const int gl = min(P.view_group, P.n_views - v0);
+        const int view = v0 + r % gl, tile = r / gl;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        switch (P.kind & 3) {
+        case GJP_F32: batch_item_i<float, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
+        case GJP_BF16: batch_item_i<__nv_bfloat16, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
+        default: batch_item_i<__half, ANY_I64, ANY_SPL>(P, tile, view, warp, lane); break;
         }
     }
 }
@@ -182,7 +191,7 @@ gjp_status launch(const gjp_batch *b, const BatchProblem *d_probs, const long lo
                   cudaStream_t s)
 {
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return GJP_ERR_CUDA;
-    b->kernel<<<b->grid, kBatchThreads, 0, s>>>(d_probs, d_begins, n, b->d_counter, kBatchChunk);
+    b->kernel<<<b->grid, kBatchThreads, kBatchRowBytes, s>>>(d_probs, d_begins, n, b->d_counter, kBatchChunk);
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
@@ -285,8 +294,9 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
         any_spl = any_spl || (P.kind & 8);
     }
     b->kernel = batch_kernel(any_i64, any_spl);
+    fit_carveout((const void *)b->kernel, kBatchThreads, kBatchRowBytes);
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kernel, kBatchThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kernel, kBatchThreads, kBatchRowBytes) !=
             cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || per_sm < 1) {
         free_batch(b);

@@ -57,10 +57,11 @@ struct VolParams {
 #define GJP_ADJOINT_AUTO GJP_PATH_COMBINE   // adjoint family taken by GJP_PATH_AUTO
 #endif
 #ifndef GJP_VIEW_GROUP
-#define GJP_VIEW_GROUP 8   // default launch order: 8 views per detector tile
+#define GJP_VIEW_GROUP 16  // default launch order: 16 views per detector tile
 #endif
-// Warps whose 32 rays share their first transverse row march from a shared
-// per-warp row table (1) or each lane steps its own row position (0).
+// Warps whose 32 rays share their first transverse row step that row once
+// per warp through a shared per-warp row table (1), or each lane steps its
+// own copy (0); forward gather and warp-combined adjoint.
 #ifndef GJP_ROWS
 #define GJP_ROWS 1
 #endif
@@ -116,6 +117,13 @@ gjp_status check_sources(const gjp_geometry *g, const int64_t n[3], const double
 VolParams make_vol(const int64_t n[3], const double h[3], double fov);
 // Whether every element offset the kernels form fits a signed 32-bit integer.
 bool fits_int32(const int64_t n[3]);
+// Sets func's preferred shared-memory carveout to the smallest share that
+// still holds as many blocks of `threads` threads and `dyn_smem` dynamic
+// bytes as its registers allow, leaving the rest of each SM's unified
+// storage to the L1 cache.  (Left alone, the driver sizes the carveout for
+// the thread-limited block count even where registers allow fewer blocks.)
+// Once per function and device; a failure leaves the default in place.
+void fit_carveout(const void *func, int threads, size_t dyn_smem);
 size_t elem_size(gjp_dtype t);
 // Texture families (gjp_texture.cu): forward through the texture unit, and
 // release of an entry's texture arrays (with the entry's device current).
@@ -656,6 +664,14 @@ __device__ __forceinline__ float march_interior_rows(const T *__restrict__ vol, 
     return acc;
 }
 
+// Row tables of the row-table march: 32 entries of 8 bytes per warp slot at
+// the start of the dynamic shared memory.  Reached through this symbol (not
+// a pointer handed down) so that every table access compiles to a
+// shared-memory access.
+extern __shared__ uint4 gjp_row_tables[];
+
+__device__ __forceinline__ uint2 *row_table(int slot) { return reinterpret_cast<uint2 *>(gjp_row_tables + 16 * slot); }
+
 __device__ __forceinline__ int lane_id()
 {
     int l;
@@ -670,7 +686,7 @@ __device__ __forceinline__ int lane_id()
 template <typename T, typename Index, bool SPL>
 __device__ __forceinline__ float forward_ray(const T *__restrict__ vol, const VolParams &V,
                                              const ViewParams *__restrict__ view, int nu, int nv, int iu, int iv,
-                                             unsigned act, uint2 *__restrict__ rows = nullptr)
+                                             unsigned act, int rows_slot = -1)
 {
     ViewParams vp;
     load_view(view, 0, vp);
@@ -691,11 +707,11 @@ __device__ __forceinline__ float forward_ray(const T *__restrict__ vol, const Vo
     const float bsum = march_boundary<T, Index, SPL>(vol, R);
     if constexpr (std::is_same<Index, int>::value) {
         // a full warp with one common row: the shared row table
-        if (GJP_ROWS && rows != nullptr && act == 0xffffffffu) {
+        if (GJP_ROWS && rows_slot >= 0 && act == 0xffffffffu) {
             const int m0 = __shfl_sync(act, R.m, 0);
             const long long Pa0 = __shfl_sync(act, R.Pa, 0), Ga0 = __shfl_sync(act, R.Ga, 0);
             if (__all_sync(act, R.m == m0 && R.Pa == Pa0 && R.Ga == Ga0) && m0 != 2)
-                return (march_interior_rows<T, SPL>(vol, R, rev, rows, lane_id()) + bsum) * R.step;
+                return (march_interior_rows<T, SPL>(vol, R, rev, row_table(rows_slot), lane_id()) + bsum) * R.step;
         }
     }
     const float acc = (R.m != 2) ? march_interior<T, Index, true, SPL>(vol, R, rev)

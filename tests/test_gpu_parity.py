@@ -255,7 +255,7 @@ def test_launch_shape_changes_no_result(gjp):
     cg = synth.cone_angle_geometry(41, 45, 7, 10.0)
     vol = torch.from_numpy(rng.random(vg.n, dtype=np.float32)).cuda()
     g = gjp.Geometry.from_cone(cg)
-    assert g.launch == (4, 8)
+    assert g.launch == (4, 16)
     base = gjp.forward(vol, g, vg.h, path="gather").clone()
     for launch in ((1, 1), (2, 5), (8, 7), (8, 64)):
         g.set_launch(*launch)
