@@ -662,35 +662,45 @@ __device__ __forceinline__ void red_add_if(bool w, float *p, float v)
 }
 
 // What one lane adds to voxels ib (x0, when w0) and ib + 1 (x1, when w1) of
-// both rows, given its taps g0 (to ib) and g1 (to ib + 1); see above.
-template <bool RUNS>
+// both rows, given its taps g0 (to ib) and g1 (to ib + 1); see above.  ASC:
+// the warp's z indices ascend with the lane index (else they descend, as for
+// detector rows along -z); the run form walks the lanes in z order.
+template <bool RUNS, bool ASC>
 __device__ __forceinline__ void combine_lane(int ib, float g0, float g1, float &x0, float &x1, bool &w0, bool &w1)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x;
-    const int ib_up = __shfl_up_sync(full, ib, 1);
-    const float g1_up = __shfl_up_sync(full, g1, 1);
-    const int ib_dn = __shfl_down_sync(full, ib, 1);
     if (RUNS) {
         // At most two neighbouring lanes share a voxel (checked once per
         // warp).  A run is one lane or two lanes on one voxel; its first lane
-        // adds the run's lower taps plus, when the previous run's voxel is
-        // the one just below, that run's upper taps; a run's last lane adds
-        // the run's upper taps itself only when no next run starts on that
-        // voxel.  Every voxel then has one writer.
-        const int dn = lane < 31 ? ib_dn - ib : 2;   // last lane: no next run
-        const int up = lane > 0 ? ib - ib_up : 2;    // first lane: no previous run
-        const float g0_dn = __shfl_down_sync(full, g0, 1);
-        const float e1 = up == 0 ? g1 + g1_up : g1;  // the run's upper taps, at its last lane
-        const float e1_up = __shfl_up_sync(full, e1, 1);
-        const float s0 = dn == 0 ? g0 + g0_dn : g0;  // the run's lower taps, at its first lane
-        x0 = up == 1 ? s0 + e1_up : s0;
+        // (in z order) adds the run's lower taps plus, when the previous
+        // run's voxel is the one just below, that run's upper taps; a run's
+        // last lane adds the run's upper taps itself only when no next run
+        // starts on that voxel.  Every voxel then has one writer.
+        // the z-previous and z-next lanes (a lane at the warp's end gets its
+        // own value back, which the has_prev / has_next tests then ignore)
+        const auto from_prev = [full](auto v) { return ASC ? __shfl_up_sync(full, v, 1) : __shfl_down_sync(full, v, 1); };
+        const auto from_next = [full](auto v) { return ASC ? __shfl_down_sync(full, v, 1) : __shfl_up_sync(full, v, 1); };
+        const bool has_prev = ASC ? lane > 0 : lane < 31, has_next = ASC ? lane < 31 : lane > 0;
+        const int ib_p = from_prev(ib);
+        const float g1_p = from_prev(g1);
+        const int ib_n = from_next(ib);
+        const int dn = has_next ? ib_n - ib : 2;      // z-last lane: no next run
+        const int up = has_prev ? ib - ib_p : 2;      // z-first lane: no previous run
+        const float g0_n = from_next(g0);
+        const float e1 = up == 0 ? g1 + g1_p : g1;    // the run's upper taps, at its last lane
+        const float e1_p = from_prev(e1);
+        const float s0 = dn == 0 ? g0 + g0_n : g0;    // the run's lower taps, at its first lane
+        x0 = up == 1 ? s0 + e1_p : s0;
         x1 = e1;
-        w0 = up != 0;                                // first lane of its run
-        w1 = (unsigned)dn > 1u;                      // last lane, and no next run on voxel ib + 1
+        w0 = up != 0;                                 // first lane of its run
+        w1 = (unsigned)dn > 1u;                       // last lane, and no next run on voxel ib + 1
     } else {
         // the previous lane's upper tap joins this lane's lower tap when they
         // are the same voxel (lane 0 receives its own values: never taken)
+        const int ib_up = __shfl_up_sync(full, ib, 1);
+        const float g1_up = __shfl_up_sync(full, g1, 1);
+        const int ib_dn = __shfl_down_sync(full, ib, 1);
         x0 = ib_up + 1 == ib ? g0 + g1_up : g0;
         x1 = g1;
         w0 = x0 != 0.0f;
@@ -701,7 +711,7 @@ __device__ __forceinline__ void combine_lane(int ib, float g0, float g1, float &
 // One plane of the warp-combined adjoint (see above).  CHECKED tests each
 // tap against the grid (zero border) and, with CLIP, the plane against the
 // ray's clipped support; unchecked planes are interior for every lane.
-template <typename Index, bool SPL, bool CHECKED, bool CLIP, bool RUNS>
+template <typename Index, bool SPL, bool CHECKED, bool CLIP, bool RUNS, bool ASC>
 __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, unsigned long long &pa,
                                               unsigned long long &pb, Index &plane, Index sa, unsigned na,
                                               unsigned nb, float *__restrict__ vol)
@@ -713,7 +723,7 @@ __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, uns
     const float g0 = __fmaf_rn(-yi, db, yi);       // yi (1 - db), to voxel ib
     float x0, x1;
     bool w0, w1;                                     // this lane adds to voxel ib / ib + 1
-    combine_lane<RUNS>(ib, g0, g1, x0, x1, w0, w1);
+    combine_lane<RUNS, ASC>(ib, g0, g1, x0, x1, w0, w1);
     float *p = vol + (plane + (Index)ia * sa + (Index)ib);
     const float wa0 = 1.0f - da;
     if (CHECKED) {
@@ -734,7 +744,7 @@ __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, uns
 
 // One unchecked plane whose row weight and row offset come from the warp's
 // row table (entry weight bits, offset).
-template <bool SPL, bool RUNS>
+template <bool SPL, bool RUNS, bool ASC>
 __device__ __forceinline__ void combine_row_plane(float yw, unsigned wbits, unsigned off, unsigned long long &pb,
                                                   unsigned long long gb, int sa, float *__restrict__ vol)
 {
@@ -744,7 +754,7 @@ __device__ __forceinline__ void combine_row_plane(float yw, unsigned wbits, unsi
     const float g0 = __fmaf_rn(-yw, db, yw);
     float x0, x1;
     bool w0, w1;
-    combine_lane<RUNS>(ib, g0, g1, x0, x1, w0, w1);
+    combine_lane<RUNS, ASC>(ib, g0, g1, x0, x1, w0, w1);
     float *p = vol + (int)(off + (unsigned)ib);
     const float da = __uint_as_float(wbits), wa0 = 1.0f - da;
     red_add2_if(w0, p, wa0 * x0, p + sa, da * x0);
@@ -756,7 +766,7 @@ __device__ __forceinline__ void combine_row_plane(float yw, unsigned wbits, unsi
 // row position is stepped once per plane for the whole warp, as in the
 // forward's row-table march -- lane k fills the entry of the k-th of the
 // next 32 planes, and every lane reads them from shared memory.
-template <bool SPL, bool RUNS>
+template <bool SPL, bool RUNS, bool ASC>
 __device__ __forceinline__ void combine_rows(const Ray &R, int i_lo, int i_hi, float yw, unsigned long long &pb,
                                              uint2 *__restrict__ rows, float *__restrict__ vol)
 {
@@ -778,14 +788,41 @@ __device__ __forceinline__ void combine_rows(const Ray &R, int i_lo, int i_hi, f
         int j = 0;
         for (; j + 1 < n; j += 2) {
             const uint4 e = *reinterpret_cast<const uint4 *>(rows + j);
-            combine_row_plane<SPL, RUNS>(yw, e.x, e.y, pb, gb, sa, vol);
-            combine_row_plane<SPL, RUNS>(yw, e.z, e.w, pb, gb, sa, vol);
+            combine_row_plane<SPL, RUNS, ASC>(yw, e.x, e.y, pb, gb, sa, vol);
+            combine_row_plane<SPL, RUNS, ASC>(yw, e.z, e.w, pb, gb, sa, vol);
         }
         if (j < n) {
             const uint2 e = rows[j];
-            combine_row_plane<SPL, RUNS>(yw, e.x, e.y, pb, gb, sa, vol);
+            combine_row_plane<SPL, RUNS, ASC>(yw, e.x, e.y, pb, gb, sa, vol);
         }
     }
+}
+
+// The warp's planes I0 .. I1: checked planes before c_end, the planes
+// F0 .. F1 that are interior for every lane unchecked (through the row
+// table with 32-bit offsets), then checked planes to the end.
+template <typename Index, bool SPL, bool CLIP, bool RUNS, bool ASC, bool USE_ROWS>
+__device__ __forceinline__ void combine_march(const Ray &R, int I0, int I1, int c_end, int F0, int F1, float yw,
+                                              unsigned long long pa, unsigned long long pb, Index plane, Index sa,
+                                              unsigned na, unsigned nb, uint2 *__restrict__ rows,
+                                              float *__restrict__ vol)
+{
+    int i = I0;
+    for (; i < c_end; ++i)
+        combine_plane<Index, SPL, true, CLIP, RUNS, ASC>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+    if (F0 <= F1) {
+        const int hi = min(F1, I1);
+        if (USE_ROWS && i <= hi) {
+            combine_rows<SPL, RUNS, ASC>(R, i, hi, yw, pb, rows, vol);
+            i = hi + 1;
+            pa = (unsigned long long)pos_at(R.Pa, R.Ga, i, R.ic);
+            plane = (Index)i * (Index)R.sm;
+        }
+        for (; i <= hi; ++i)
+            combine_plane<Index, SPL, false, false, RUNS, ASC>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+    }
+    for (; i <= I1; ++i)
+        combine_plane<Index, SPL, true, CLIP, RUNS, ASC>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
 }
 
 template <typename Index, bool SPL, bool CLIP>
@@ -848,7 +885,7 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
     // apart differ by at least one voxel, with one sign, on the first and the
     // last plane (the difference is affine in the plane index, so it then
     // holds in between).
-    bool runs_ok = true;
+    bool runs_ok = true, asc = true;
     {
         const long long one = 1LL << 32;
         long long d[2];
@@ -859,41 +896,17 @@ __global__ void __launch_bounds__(kMaxThreads) gjp_adjoint_combine_kernel(
         }
         if (lane < 30 && !((d[0] >= one && d[1] >= one) || (d[0] <= -one && d[1] <= -one))) runs_ok = false;
         runs_ok = __all_sync(full, runs_ok);
+        asc = __shfl_sync(full, d[0] > 0 ? 1 : 0, 0) != 0;   // z order of the lanes (used by the run form)
     }
-    int i = I0;
-    if (runs_ok) {
-        for (; i < c_end; ++i)
-            combine_plane<Index, SPL, true, CLIP, true>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
-        if (F0 <= F1) {
-            const int hi = min(F1, I1);
-            if (USE_ROWS && i <= hi) {
-                combine_rows<SPL, true>(R, i, hi, yw, pb, rows, vol);
-                i = hi + 1;
-                pa = (unsigned long long)pos_at(R.Pa, R.Ga, i, R.ic);
-                plane = (Index)i * sm;
-            }
-            for (; i <= hi; ++i)
-                combine_plane<Index, SPL, false, false, true>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
-        }
-        for (; i <= I1; ++i)
-            combine_plane<Index, SPL, true, CLIP, true>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
-        return;
-    }
-    for (; i < c_end; ++i)
-        combine_plane<Index, SPL, true, CLIP, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
-    if (F0 <= F1) {
-        const int hi = min(F1, I1);
-        if (USE_ROWS && i <= hi) {
-            combine_rows<SPL, false>(R, i, hi, yw, pb, rows, vol);
-            i = hi + 1;
-            pa = (unsigned long long)pos_at(R.Pa, R.Ga, i, R.ic);
-            plane = (Index)i * sm;
-        }
-        for (; i <= hi; ++i)
-            combine_plane<Index, SPL, false, false, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
-    }
-    for (; i <= I1; ++i)
-        combine_plane<Index, SPL, true, CLIP, false>(R, i, yw, pa, pb, plane, sa, na, nb, vol);
+    if (!runs_ok)
+        combine_march<Index, SPL, CLIP, false, true, USE_ROWS>(R, I0, I1, c_end, F0, F1, yw, pa, pb, plane, sa, na, nb,
+                                                               rows, vol);
+    else if (asc)
+        combine_march<Index, SPL, CLIP, true, true, USE_ROWS>(R, I0, I1, c_end, F0, F1, yw, pa, pb, plane, sa, na, nb,
+                                                              rows, vol);
+    else
+        combine_march<Index, SPL, CLIP, true, false, USE_ROWS>(R, I0, I1, c_end, F0, F1, yw, pa, pb, plane, sa, na, nb,
+                                                               rows, vol);
 }
 
 // ---------------------------------------------------------------------------
