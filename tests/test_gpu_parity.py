@@ -315,6 +315,29 @@ def test_dot_test_differentiation_workload(gjp):
         assert abs(lhs - rhs) <= 1e-5 * scale, (kind, lhs, rhs, scale)
 
 
+def test_adjoint_rows_along_minus_z_full_size(gjp):
+    """Detector rows along -z on the 256^3 / 180-view / 256^2 workload: each
+    warp's z indices fall lane by lane, so the combined adjoint walks its
+    runs against the lane order.  It must agree with the tap-by-tap scatter
+    (the same transpose, summed in another order) and pass the dot test."""
+    vg, cg = synth.c4_geometry()
+    cg.det_origin = cg.det_origin + (cg.nv - 1) * cg.det_v
+    cg.det_v = -cg.det_v
+    g = gjp.Geometry.from_cone(cg)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    x = torch.rand(vg.n, device="cuda", generator=gen)
+    y = torch.rand(cg.n_views, cg.nv, cg.nu, device="cuda", generator=gen)
+    aty = gjp.adjoint(y, g, vg.n, voxel_size=vg.h, path="combine")
+    ref = gjp.adjoint(y, g, vg.n, voxel_size=vg.h, path="gather")
+    gjp.stream_status()
+    assert ((aty - ref).abs().max() / ref.abs().max()).item() < 1e-5
+    ax = gjp.forward(x, g, voxel_size=vg.h)
+    lhs = torch.sum(ax.double() * y.double()).item()
+    rhs = torch.sum(x.double() * aty.double()).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
 def test_gradient_finite_differences_differentiation_workload(gjp):
     """L(x) = 1/2 |A x - b|^2 is quadratic, so central differences equal
     (A e_j)^T (A x - b) exactly; compare with the adjoint's A^T (A x - b) on
