@@ -73,6 +73,7 @@ constexpr int kTileU = GJP_TILE_U;  // default warps of a block along u
 constexpr int kMaxTileU = GJP_MAX_TILE_U;   // largest block: 8 warps
 constexpr int kMaxThreads = kTileV * kMaxTileU;
 constexpr int kBatch = GJP_BATCH;   // interior planes per batch
+static_assert(kBatch % 2 == 0, "interior batches are evaluated two planes at a time");
 // register budget of the one-thread-per-ray kernels: the same per-thread
 // limit as GJP_MIN_BLOCKS resident blocks of 4 warps
 constexpr int kMinBlocksMax = (GJP_MIN_BLOCKS * 4 + kMaxTileU - 1) / kMaxTileU;
@@ -225,6 +226,82 @@ template <> __device__ __forceinline__ float load_voxel<__half>(const __half *p)
 __device__ __forceinline__ float to_float(float x) { return x; }
 __device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
+
+// ---------------------------------------------------------------------------
+// Eq. 12 on packed FP32 pairs.  The interior marches evaluate two samples
+// (planes t and t + 1 of a ray) per instruction with the paired FP32
+// operations of sm_100+ (FFMA2), which halves the issue slots of the
+// interpolation.  A 16-bit voxel stays in its storage word until the
+// z-interpolation: the lower tap is widened (exact), and the difference to
+// the upper tap is one mixed-precision subtraction (sub.f32.bf16 /
+// sub.f32.f16: the 16-bit operand is widened exactly, one rounding), so
+// weights and sums stay FP32 and the results equal those of widening every
+// tap first.
+
+template <typename T> struct Raw { using type = float; };
+template <> struct Raw<__nv_bfloat16> { using type = unsigned short; };
+template <> struct Raw<__half> { using type = unsigned short; };
+
+template <typename T> __device__ __forceinline__ typename Raw<T>::type load_raw(const T *p)
+{
+    if constexpr (std::is_same<T, float>::value) return __ldg(p);
+    else return __ldg(reinterpret_cast<const unsigned short *>(p));
+}
+
+template <typename T> __device__ __forceinline__ float widen(typename Raw<T>::type x)
+{
+    if constexpr (std::is_same<T, float>::value) return x;
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __uint_as_float((unsigned)x << 16);
+    else return __half2float(__ushort_as_half(x));
+}
+
+// b - a, rounded once, for a stored voxel b and an FP32 a
+template <typename T> __device__ __forceinline__ float sub_raw(typename Raw<T>::type b, float a)
+{
+    float r;
+    if constexpr (std::is_same<T, float>::value) r = __fsub_rn(b, a);
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value) asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(b), "f"(a));
+    else asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(b), "f"(a));
+    return r;
+}
+
+// Upper-neighbour weights (Eq. 10, 13/14) of two fixed-point positions.
+template <bool SPL> __device__ __forceinline__ float2 upper_weight2(unsigned long long p, unsigned long long q)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 d = __fadd2_rn(make_float2(__uint_as_float(__funnelshift_r((unsigned)p, 0x7Fu, 9)),
+                                            __uint_as_float(__funnelshift_r((unsigned)q, 0x7Fu, 9))),
+                                m1);
+    if (!SPL) return d;
+    // 3d^2 - 2d^3 = d^2 (3 - 2d)
+    return __fmul2_rn(__fmul2_rn(d, d), __ffma2_rn(d, make_float2(-2.0f, -2.0f), make_float2(3.0f, 3.0f)));
+}
+
+// Two samples of Eq. 12: taps (v00, v01) on the lower transverse row (lower
+// and upper z), (v10, v11) on the upper row, for samples x and y of the
+// pair; da / db the upper-neighbour weights of the row and z axes.
+template <typename T>
+__device__ __forceinline__ float2 eq12_pair(typename Raw<T>::type v00x, typename Raw<T>::type v00y,
+                                            typename Raw<T>::type v01x, typename Raw<T>::type v01y,
+                                            typename Raw<T>::type v10x, typename Raw<T>::type v10y,
+                                            typename Raw<T>::type v11x, typename Raw<T>::type v11y, float2 da,
+                                            float2 db)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 a0 = make_float2(widen<T>(v00x), widen<T>(v00y));
+    const float2 a1 = make_float2(widen<T>(v10x), widen<T>(v10y));
+    float2 d0, d1;
+    if constexpr (std::is_same<T, float>::value) {
+        d0 = __ffma2_rn(a0, m1, make_float2(v01x, v01y));   // v01 - v00
+        d1 = __ffma2_rn(a1, m1, make_float2(v11x, v11y));
+    } else {
+        d0 = make_float2(sub_raw<T>(v01x, a0.x), sub_raw<T>(v01y, a0.y));
+        d1 = make_float2(sub_raw<T>(v11x, a1.x), sub_raw<T>(v11y, a1.y));
+    }
+    const float2 e0 = __ffma2_rn(db, d0, a0);                 // lower row, interpolated along z
+    const float2 e1 = __ffma2_rn(db, d1, a1);                 // upper row
+    return __ffma2_rn(da, __ffma2_rn(e0, m1, e1), e0);      // between the rows
+}
 
 // ---------------------------------------------------------------------------
 // Per-ray setup.
@@ -429,6 +506,40 @@ __device__ __forceinline__ void block_tile_view(int n_views, int view_group, int
 // Forward projection: one thread per ray; a block is blockDim.y detector
 // columns x 32 rows (v-tiles fastest within a view).
 
+// One batch of kBatch interior planes of a ray (no checks): gathers the
+// 4 kBatch taps first, then evaluates Eq. 12 two planes at a time; returns
+// the batch sum as an FP32 pair (even and odd planes).
+template <typename T, typename Index, bool SPL>
+__device__ __forceinline__ float2 interior_batch(const T *__restrict__ vol, unsigned long long &pa,
+                                                 unsigned long long &pb, Index &plane, unsigned long long ga,
+                                                 unsigned long long gb, Index sa, Index sb, Index sm)
+{
+    using W = typename Raw<T>::type;
+    W v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch];
+    unsigned long long qa[kBatch], qb[kBatch];
+#pragma unroll
+    for (int t = 0; t < kBatch; ++t) {
+        qa[t] = pa;
+        qb[t] = pb;
+        const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
+        v00[t] = load_raw(p);
+        v01[t] = load_raw(p + sb);
+        v10[t] = load_raw(p + sa);
+        v11[t] = load_raw(p + sa + sb);
+        pa += ga;
+        pb += gb;
+        plane += sm;
+    }
+    float2 bsum = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int t = 0; t < kBatch; t += 2) {
+        const float2 da = upper_weight2<SPL>(qa[t], qa[t + 1]), db = upper_weight2<SPL>(qb[t], qb[t + 1]);
+        bsum = __fadd2_rn(bsum, eq12_pair<T>(v00[t], v00[t + 1], v01[t], v01[t + 1], v10[t], v10[t + 1], v11[t],
+                                             v11[t + 1], da, db));
+    }
+    return bsum;
+}
+
 // Interior planes j_lo .. j_hi of one ray: all four taps lie inside the
 // grid, so no checks.  rev marches the same planes from j_hi down to j_lo
 // (a warp picks the direction in which its lanes start on a common plane,
@@ -449,64 +560,21 @@ __device__ __forceinline__ float march_interior(const T *__restrict__ vol, const
     Index plane = (Index)i0 * (Index)R.sm;
     // two-level sum: planes of a batch are added together, four batch sums
     // make a block sum, and block sums join the total once per 16 planes
-    // (float32 error ~4x smaller than a running sum over up to ~n_m planes)
-    float acc = 0.0f;
+    // (float32 error ~4x smaller than a running sum over up to ~n_m planes);
+    // the partial sums are FP32 pairs (even and odd planes)
+    float2 acc = make_float2(0.0f, 0.0f);
     for (; count >= 4 * kBatch; count -= 4 * kBatch) {
-        float blk = 0.0f;
+        float2 blk = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                da[t] = upper_weight<SPL>(frac_of(pa));
-                db[t] = upper_weight<SPL>(frac_of(pb));
-                const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-                v00[t] = load_voxel(p);
-                v01[t] = load_voxel(p + sb);
-                v10[t] = load_voxel(p + sa);
-                v11[t] = load_voxel(p + sa + sb);
-                pa += ga;
-                pb += gb;
-                plane += sm;
-            }
-            float bsum = 0.0f;
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                // Eq. 12 with the weights of Eq. 13/14, as two nested interpolations
-                const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
-                const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
-                bsum += __fmaf_rn(da[t], e1 - e0, e0);
-            }
-            blk += bsum;
-        }
-        acc += blk;
+        for (int q = 0; q < 4; ++q)
+            blk = __fadd2_rn(blk, interior_batch<T, Index, SPL>(vol, pa, pb, plane, ga, gb, sa, sb, sm));
+        acc = __fadd2_rn(acc, blk);
     }
-    float part = 0.0f;                               // fewer than 16 planes left
-    for (; count >= kBatch; count -= kBatch) {
-        float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t) {
-            da[t] = upper_weight<SPL>(frac_of(pa));
-            db[t] = upper_weight<SPL>(frac_of(pb));
-            const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-            v00[t] = load_voxel(p);
-            v01[t] = load_voxel(p + sb);
-            v10[t] = load_voxel(p + sa);
-            v11[t] = load_voxel(p + sa + sb);
-            pa += ga;
-            pb += gb;
-            plane += sm;
-        }
-        float bsum = 0.0f;
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t) {
-            const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
-            const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
-            bsum += __fmaf_rn(da[t], e1 - e0, e0);
-        }
-        part += bsum;
-    }
-    acc += part;
+    float2 part = make_float2(0.0f, 0.0f);           // fewer than 16 planes left
+    for (; count >= kBatch; count -= kBatch)
+        part = __fadd2_rn(part, interior_batch<T, Index, SPL>(vol, pa, pb, plane, ga, gb, sa, sb, sm));
+    acc = __fadd2_rn(acc, part);
+    float tail = 0.0f;
     for (; count > 0; --count) {
         const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
         const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
@@ -514,12 +582,12 @@ __device__ __forceinline__ float march_interior(const T *__restrict__ vol, const
         const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + sb);
         const float e0 = __fmaf_rn(db, v01 - v00, v00);
         const float e1 = __fmaf_rn(db, v11 - v10, v10);
-        acc += __fmaf_rn(da, e1 - e0, e0);
+        tail += __fmaf_rn(da, e1 - e0, e0);
         pa += ga;
         pb += gb;
         plane += sm;
     }
-    return acc;
+    return (acc.x + acc.y) + tail;
 }
 
 template <typename T, typename Index, bool SPL = false>
@@ -550,56 +618,58 @@ __device__ __forceinline__ float march_boundary(const T *__restrict__ vol, const
     return acc;
 }
 
-// One 16-plane block of the row-table march (below): entries e[0..15] give
-// each plane's row weight and row offset (read two at a time), pb steps
-// along z.  CHECKED loads only the taps of planes 0 <= d + t < cnt (this
-// lane's interior), the others contribute zero, and stops after `n` planes
-// (warp-uniform: no lane has an interior plane past them).
+// One 16-plane block of the row-table march (below): e holds, per pair of
+// planes (t, t + 1), the words (row weight t, row weight t + 1, row offset
+// t, row offset t + 1), read with one 16-byte load; pb steps along z.
+// CHECKED loads only the taps of planes 0 <= d + t < cnt (this lane's
+// interior), the others contribute zero, and stops after `n` planes
+// (warp-uniform: no lane has an interior plane past them).  Returns the
+// block sum as an FP32 pair (even and odd planes).
 template <typename T, bool SPL, bool CHECKED>
-__device__ __forceinline__ float rows_block(const T *__restrict__ vol, const uint2 *__restrict__ e,
-                                            unsigned long long &pb, unsigned long long gb, int sa, int d, int cnt,
-                                            int n)
+__device__ __forceinline__ float2 rows_block(const T *__restrict__ vol, const uint4 *__restrict__ e,
+                                             unsigned long long &pb, unsigned long long gb, int sa, int d, int cnt,
+                                             int n)
 {
-    float blk = 0.0f;
+    using W = typename Raw<T>::type;
+    float2 blk = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         if (CHECKED && q * kBatch >= n) break;
-        float v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch], da[kBatch], db[kBatch];
+        W v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch];
+        unsigned long long qb[kBatch];
+        float2 da[kBatch / 2];
         unsigned off[kBatch];
 #pragma unroll
         for (int t = 0; t < kBatch; t += 2) {
-            const uint4 en = *reinterpret_cast<const uint4 *>(e + q * kBatch + t);
-            da[t] = __uint_as_float(en.x);
-            off[t] = en.y;
-            da[t + 1] = __uint_as_float(en.z);
+            const uint4 en = e[(q * kBatch + t) / 2];
+            da[t / 2] = make_float2(__uint_as_float(en.x), __uint_as_float(en.y));
+            off[t] = en.z;
             off[t + 1] = en.w;
         }
 #pragma unroll
         for (int t = 0; t < kBatch; ++t) {
-            db[t] = upper_weight<SPL>(frac_of(pb));
+            qb[t] = pb;
             const T *p = vol + (int)(off[t] + (unsigned)floor_of(pb));
             if (CHECKED) {
                 const bool in = (unsigned)(d + q * kBatch + t) < (unsigned)cnt;
-                v00[t] = in ? load_voxel(p) : 0.0f;
-                v01[t] = in ? load_voxel(p + 1) : 0.0f;
-                v10[t] = in ? load_voxel(p + sa) : 0.0f;
-                v11[t] = in ? load_voxel(p + sa + 1) : 0.0f;
+                v00[t] = in ? load_raw(p) : W(0);
+                v01[t] = in ? load_raw(p + 1) : W(0);
+                v10[t] = in ? load_raw(p + sa) : W(0);
+                v11[t] = in ? load_raw(p + sa + 1) : W(0);
             } else {
-                v00[t] = load_voxel(p);
-                v01[t] = load_voxel(p + 1);
-                v10[t] = load_voxel(p + sa);
-                v11[t] = load_voxel(p + sa + 1);
+                v00[t] = load_raw(p);
+                v01[t] = load_raw(p + 1);
+                v10[t] = load_raw(p + sa);
+                v11[t] = load_raw(p + sa + 1);
             }
             pb += gb;
         }
-        float bsum = 0.0f;
 #pragma unroll
-        for (int t = 0; t < kBatch; ++t) {
-            const float e0 = __fmaf_rn(db[t], v01[t] - v00[t], v00[t]);
-            const float e1 = __fmaf_rn(db[t], v11[t] - v10[t], v10[t]);
-            bsum += __fmaf_rn(da[t], e1 - e0, e0);
+        for (int t = 0; t < kBatch; t += 2) {
+            const float2 db = upper_weight2<SPL>(qb[t], qb[t + 1]);
+            blk = __fadd2_rn(blk, eq12_pair<T>(v00[t], v00[t + 1], v01[t], v01[t + 1], v10[t], v10[t + 1], v11[t],
+                                               v11[t + 1], da[t / 2], db));
         }
-        blk += bsum;
     }
     return blk;
 }
@@ -615,11 +685,12 @@ __device__ __forceinline__ float rows_block(const T *__restrict__ vol, const uin
 // the warp's planes together; a 16-plane block inside every lane's interior
 // runs without checks, other blocks load only the taps of lanes whose
 // interior holds the plane (their boundary planes are summed elsewhere).
-// `rows` is this warp's 32-entry table, 16-byte aligned: (row weight bits,
-// row offset) per plane.
+// `rows` is this warp's 32-entry table (256 bytes, 16-byte aligned): per
+// pair of planes the row weight bits of both, then the row offsets of both
+// (the layout rows_block reads).
 template <typename T, bool SPL>
 __device__ __forceinline__ float march_interior_rows(const T *__restrict__ vol, const Ray &R, bool rev,
-                                                     uint2 *__restrict__ rows, int lane)
+                                                     uint4 *__restrict__ rows, int lane)
 {
     const unsigned full = 0xffffffffu;
     const bool has = R.j_lo <= R.j_hi;
@@ -644,11 +715,12 @@ __device__ __forceinline__ float march_interior_rows(const T *__restrict__ vol, 
     unsigned row = (unsigned)(i0 + dir * lane) * (unsigned)R.sm;
     const unsigned sm32 = (unsigned)(dir * 32) * (unsigned)R.sm;
 
-    float acc = 0.0f;
+    unsigned *slot = reinterpret_cast<unsigned *>(rows) + 4 * (lane >> 1) + (lane & 1);
+    float2 acc = make_float2(0.0f, 0.0f);
     for (int w = 0; w < L; w += 32) {
         __syncwarp();                                 // every lane has read the last window
-        rows[lane] = make_uint2(__float_as_uint(upper_weight<SPL>(frac_of(pa))),
-                                row + (unsigned)floor_of(pa) * (unsigned)sa);
+        slot[0] = __float_as_uint(upper_weight<SPL>(frac_of(pa)));
+        slot[2] = row + (unsigned)floor_of(pa) * (unsigned)sa;
         pa += ga32;
         row += sm32;
         __syncwarp();
@@ -656,12 +728,12 @@ __device__ __forceinline__ float march_interior_rows(const T *__restrict__ vol, 
         for (int kb = 0; kb < nw; kb += 16) {
             const int k = w + kb;
             if (k >= K0 && k + 15 <= K1)              // warp-uniform
-                acc += rows_block<T, SPL, false>(vol, rows + kb, pb, gb, sa, 0, 0, 16);
+                acc = __fadd2_rn(acc, rows_block<T, SPL, false>(vol, rows + kb / 2, pb, gb, sa, 0, 0, 16));
             else
-                acc += rows_block<T, SPL, true>(vol, rows + kb, pb, gb, sa, k - k_lo, cnt, L - k);
+                acc = __fadd2_rn(acc, rows_block<T, SPL, true>(vol, rows + kb / 2, pb, gb, sa, k - k_lo, cnt, L - k));
         }
     }
-    return acc;
+    return acc.x + acc.y;
 }
 
 // Row tables of the row-table march: 32 entries of 8 bytes per warp slot at
@@ -711,7 +783,8 @@ __device__ __forceinline__ float forward_ray(const T *__restrict__ vol, const Vo
             const int m0 = __shfl_sync(act, R.m, 0);
             const long long Pa0 = __shfl_sync(act, R.Pa, 0), Ga0 = __shfl_sync(act, R.Ga, 0);
             if (__all_sync(act, R.m == m0 && R.Pa == Pa0 && R.Ga == Ga0) && m0 != 2)
-                return (march_interior_rows<T, SPL>(vol, R, rev, row_table(rows_slot), lane_id()) + bsum) * R.step;
+                return (march_interior_rows<T, SPL>(vol, R, rev, gjp_row_tables + 16 * rows_slot, lane_id()) + bsum) *
+                       R.step;
         }
     }
     const float acc = (R.m != 2) ? march_interior<T, Index, true, SPL>(vol, R, rev)
