@@ -277,15 +277,16 @@ gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny
  * reconstruction loop that forbids allocation after acquisition starts, or a
  * plug-in that must not touch its host application's allocator.
  *
- * It computes exactly what gjp_forward computes (same gather kernels), but
+ * It computes exactly what gjp_forward computes (the same per-view table
+ * and the same gather kernels, so the projections are bitwise equal), but
  * keeps the per-view table in a fixed array of GJP_NOALLOC_MAX_VIEWS entries
  * (144 bytes each, about 144 KiB) that the CUDA runtime places on every GPU
  * that loads this library and keeps there until the process exits.  The
- * table is formed on the host (in a small stack buffer) and copied from
- * there into that array on `stream` before the kernel runs; the call
- * performs no cudaMalloc, cudaFree or other allocation.  Because the copy
- * comes from ordinary (pageable) host memory, the call may wait for work
- * already queued on `stream` before it returns.
+ * table is formed on the host and written into that array on `stream`,
+ * ahead of the projection, by a small copy kernel that receives up to 64
+ * views per launch as its by-value parameters; the call performs no
+ * cudaMalloc, cudaFree, host-to-device memcpy or other allocation, and
+ * returns without waiting for the GPU.
  *   - Geometries with more than GJP_NOALLOC_MAX_VIEWS views are rejected
  *     with GJP_ERR_UNSUPPORTED (split the views over several calls).
  *   - The first call on each device looks up the array's device address

@@ -43,33 +43,40 @@ void split(double x, float &hi, float &lo)
     lo = (float)(x - (double)hi);
 }
 
+// Host FP64 setup of view k for one volume grid (Eq. 1-2 in index units):
+// the ray direction r(u, v) = R0 + u RU + v RV from the source to the pixel
+// centre at centred pixel coordinates (u, v), and its moment M = s x r
+// about the volume centre, each split into hi + lo FP32 parts.
+void make_view_params(const gjp_geometry &g, int k, const int64_t n[3], const double h[3], const double o[3],
+                      ViewParams &vp)
+{
+    const double cu = 0.5 * (g.nu - 1), cv = 0.5 * (g.nv - 1);
+    double s[3], R[9], M[9];
+    for (int a = 0; a < 3; ++a) {
+        const double c = 0.5 * (double)(n[a] - 1);
+        s[a] = (g.src[3 * k + a] - o[a]) / h[a] - c;                         // source, centred index units
+        R[3 + a] = g.du[3 * k + a] / h[a];
+        R[6 + a] = g.dv[3 * k + a] / h[a];
+        R[a] = (g.org[3 * k + a] - g.src[3 * k + a]) / h[a] + cu * R[3 + a] + cv * R[6 + a];
+    }
+    for (int t = 0; t < 3; ++t) {                                             // M = s x R (columns 0,1,2)
+        const double *x = R + 3 * t;
+        M[3 * t + 0] = s[1] * x[2] - s[2] * x[1];
+        M[3 * t + 1] = s[2] * x[0] - s[0] * x[2];
+        M[3 * t + 2] = s[0] * x[1] - s[1] * x[0];
+    }
+    for (int j = 0; j < 9; ++j) {
+        split(R[j], vp.rh[j], vp.rl[j]);
+        split(M[j], vp.mh[j], vp.ml[j]);
+    }
+}
+
 // Host FP64 construction of the per-view table for one volume grid.
 void build_table(const gjp_geometry &g, const int64_t n[3], const double h[3], const double o[3],
                  std::vector<ViewParams> &out)
 {
     out.resize(g.n_views);
-    const double cu = 0.5 * (g.nu - 1), cv = 0.5 * (g.nv - 1);
-    for (int k = 0; k < g.n_views; ++k) {
-        double s[3], R[9], M[9];
-        for (int a = 0; a < 3; ++a) {
-            const double c = 0.5 * (double)(n[a] - 1);
-            s[a] = (g.src[3 * k + a] - o[a]) / h[a] - c;                     // source, centred index units
-            R[3 + a] = g.du[3 * k + a] / h[a];
-            R[6 + a] = g.dv[3 * k + a] / h[a];
-            R[a] = (g.org[3 * k + a] - g.src[3 * k + a]) / h[a] + cu * R[3 + a] + cv * R[6 + a];
-        }
-        for (int t = 0; t < 3; ++t) {                                         // M = s x R (columns 0,1,2)
-            const double *x = R + 3 * t;
-            M[3 * t + 0] = s[1] * x[2] - s[2] * x[1];
-            M[3 * t + 1] = s[2] * x[0] - s[0] * x[2];
-            M[3 * t + 2] = s[0] * x[1] - s[1] * x[0];
-        }
-        ViewParams &vp = out[k];
-        for (int j = 0; j < 9; ++j) {
-            split(R[j], vp.rh[j], vp.rl[j]);
-            split(M[j], vp.mh[j], vp.ml[j]);
-        }
-    }
+    for (int k = 0; k < g.n_views; ++k) make_view_params(g, k, n, h, o, out[k]);
 }
 
 // Returns the cache entry (device table) for (g, current device, grid);
@@ -1550,6 +1557,22 @@ bool try_adjoint_slab(const float *proj, const int64_t n[3], const double h[3], 
 constexpr int kNoAllocMaxViews = GJP_NOALLOC_MAX_VIEWS;
 static __device__ __align__(256) unsigned char g_noalloc_table[kNoAllocMaxViews * sizeof(ViewParams)];
 
+// The table reaches the array as the by-value parameters of a small copy
+// kernel, a chunk of views per launch (9 KiB of parameters; the launch
+// takes its own copy of them, so no host buffer has to outlive the call).
+constexpr int kNoAllocChunk = 64;
+struct NoAllocChunk {
+    ViewParams v[kNoAllocChunk];
+};
+
+__global__ void gjp_noalloc_fill_kernel(const __grid_constant__ NoAllocChunk c, int k0, int cnt)
+{
+    const unsigned *src = reinterpret_cast<const unsigned *>(c.v);
+    unsigned *dst = reinterpret_cast<unsigned *>(reinterpret_cast<ViewParams *>(g_noalloc_table) + k0);
+    const int words = cnt * (int)(sizeof(ViewParams) / sizeof(unsigned));
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
 // Host side: device address of g_noalloc_table for each device, looked up
 // once per device (with that device current) by the first call there.
 constexpr int kNoAllocMaxDevices = 64;
@@ -1741,40 +1764,16 @@ gjp_status gjp_forward_noalloc(const void *d_volume, gjp_dtype dtype, int64_t nx
     ViewParams *d_table = nullptr;
     if ((st = noalloc_table_address(dev, &d_table)) != GJP_OK) return st;
 
-    // the per-view table is formed on the host in a small stack buffer, a
-    // chunk of views at a time, and copied into the fixed device array on the
-    // caller's stream ahead of the kernel that reads it (a copy from pageable
-    // memory has consumed its source when cudaMemcpyAsync returns)
+    // the per-view table is formed on the host, a chunk of views at a time,
+    // and written into the fixed device array by a copy kernel on the
+    // caller's stream ahead of the kernel that reads it
     cudaStream_t s = (cudaStream_t)stream;
-    constexpr int kChunk = 32;
-    ViewParams chunk[kChunk];
-    const double cu = 0.5 * (g->nu - 1), cv = 0.5 * (g->nv - 1);
-    for (int k0 = 0; k0 < g->n_views; k0 += kChunk) {
-        const int cnt = std::min(kChunk, g->n_views - k0);
-        for (int j = 0; j < cnt; ++j) {
-            const int k = k0 + j;
-            double sc[3], R[9], M[9];
-            for (int a = 0; a < 3; ++a) {
-                const double c = 0.5 * (double)(n[a] - 1);
-                sc[a] = (g->src[3 * k + a] - o[a]) / h[a] - c;
-                R[3 + a] = g->du[3 * k + a] / h[a];
-                R[6 + a] = g->dv[3 * k + a] / h[a];
-                R[a] = (g->org[3 * k + a] - g->src[3 * k + a]) / h[a] + cu * R[3 + a] + cv * R[6 + a];
-            }
-            for (int t = 0; t < 3; ++t) {
-                const double *x = R + 3 * t;
-                M[3 * t + 0] = sc[1] * x[2] - sc[2] * x[1];
-                M[3 * t + 1] = sc[2] * x[0] - sc[0] * x[2];
-                M[3 * t + 2] = sc[0] * x[1] - sc[1] * x[0];
-            }
-            for (int q = 0; q < 9; ++q) {
-                split(R[q], chunk[j].rh[q], chunk[j].rl[q]);
-                split(M[q], chunk[j].mh[q], chunk[j].ml[q]);
-            }
-        }
-        if (cudaMemcpyAsync(d_table + k0, chunk, sizeof(ViewParams) * (size_t)cnt, cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
-            return GJP_ERR_CUDA;
+    NoAllocChunk chunk;
+    for (int k0 = 0; k0 < g->n_views; k0 += kNoAllocChunk) {
+        const int cnt = std::min(kNoAllocChunk, g->n_views - k0);
+        for (int j = 0; j < cnt; ++j) make_view_params(*g, k0 + j, n, h, o, chunk.v[j]);
+        gjp_noalloc_fill_kernel<<<1, 256, 0, s>>>(chunk, k0, cnt);
+        if (cudaGetLastError() != cudaSuccess) return GJP_ERR_CUDA;
     }
     const VolParams V = make_vol(n, h, g->fov);
     const bool i32 = fits_int32(n);
