@@ -70,3 +70,75 @@ def test_two_gloo_ranks():
         assert (lo, hi) == (1, 1)           # every view owned by exactly one rank
         assert tmax == 11.0
         assert total == 360.0
+
+
+# --- one scan split by views (ShardedScan), gloo ranks on CPU -----------------
+# The per-rank projector is the FP64 oracle here (CPU ranks have no GPU); the
+# test checks the split itself: shards, the gather of the projections and the
+# all-reduce of the adjoint volume against one unsplit oracle call.
+
+def _small_case(n_views):
+    import synth
+    from synth.geometry import VolumeGeometry
+    vg = VolumeGeometry.centred((14, 12, 10), h=(1.0, 0.9, 1.1))
+    cone = synth.circular(n_views, 12, 10, 60.0, 120.0, 1.7)
+    return vg, cone
+
+
+def _oracle_callables(vg):
+    import numpy as np
+    import oracle
+
+    def fwd(volume, cone, voxel_size, origin, out, stream):
+        return torch.from_numpy(oracle.forward(volume.numpy(), vg, cone, threads=1))
+
+    def adj(proj, cone, shape, voxel_size, origin, out, stream):
+        return torch.from_numpy(oracle.adjoint(proj.numpy().astype(np.float64), vg, cone, threads=1))
+
+    return (lambda cone: cone), fwd, adj
+
+
+def _scan_worker(rank, world, port, n_views, q):
+    import numpy as np
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        vg, cone = _small_case(n_views)
+        vol = torch.from_numpy(np.random.default_rng(3).random(vg.n))
+        mk, fwd, adj = _oracle_callables(vg)
+        scan = gdist.ShardedScan(cone, make_geometry=mk, forward_fn=fwd, adjoint_fn=adj)
+        local = scan.forward(vol, vg.h).to(torch.float64)
+        full = scan.gather(local.float())
+        back = scan.adjoint(local, vg.n, vg.h)
+        q.put((rank, scan.start, scan.stop, full.numpy(), back.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,n_views", [(2, 7), (3, 2)])
+def test_sharded_scan_equals_one_unsplit_scan(world, n_views):
+    import numpy as np
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_scan_worker, args=(r, world, port, n_views, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    outs = sorted((q.get(timeout=120) for _ in range(world)), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    vg, cone = _small_case(n_views)
+    vol = np.random.default_rng(3).random(vg.n)
+    ref = oracle.forward(vol, vg, cone, threads=1)
+    ref_back = oracle.adjoint(ref, vg, cone, threads=1)
+    covered = np.zeros(n_views, dtype=int)
+    for rank, start, stop, full, back in outs:
+        covered[start:stop] += 1
+        # every rank holds the whole scan's projections, in view order
+        np.testing.assert_array_equal(full, ref.astype(np.float32))
+        # and the whole A^T y: the sum of the ranks' view blocks
+        assert np.abs(back - ref_back).max() <= 1e-12 * np.abs(ref_back).max()
+    assert (covered == 1).all()
