@@ -204,7 +204,10 @@ gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int
  * gjp_stream_status -- synchronises `stream` and reports whether any kernel
  * of this library gave up a bounded wait since the last call
  * (GJP_ERR_TIMEOUT; the flag is then cleared).  Such a kernel returns
- * without hanging the device but its output is not valid.
+ * without hanging the device but its output is not valid.  A library built
+ * with GJP_CHECK_TAPS=1 also reports GJP_ERR_INTERNAL (taking precedence)
+ * when a kernel met a tap outside the grid in a plane range it marches
+ * without per-tap tests (see gjp_selftest_tap_check).
  */
 gjp_status gjp_stream_status(void *stream);
 
@@ -218,6 +221,20 @@ gjp_status gjp_stream_status(void *stream);
  * context stays usable.  Touches no caller memory.
  */
 gjp_status gjp_selftest_wait_timeout(void *stream);
+
+/*
+ * gjp_selftest_tap_check -- self-test of the debug build (the paper has no
+ * counterpart).  A library compiled with GJP_CHECK_TAPS=1 range-checks every
+ * tap that the interior plane marches (Algorithm 1's loop over the planes
+ * whose four Eq. 12 taps all lie in the grid) read or reduce without a
+ * per-tap test: a tap outside the grid is skipped, not accessed, and
+ * recorded, and the next gjp_stream_status reports GJP_ERR_INTERNAL (once;
+ * the record is cleared).  This call queues on `stream` one thread that
+ * records such a tap through the same check, touching no memory, so that a
+ * test can see the report path work.  Returns GJP_ERR_UNSUPPORTED in the
+ * production build, which has no check.
+ */
+gjp_status gjp_selftest_tap_check(void *stream);
 
 /*
  * gjp_adjoint -- matched transpose of gjp_forward (float32 volume):

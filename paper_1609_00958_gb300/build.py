@@ -14,6 +14,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("gjp.cu", "gjp_batch.cu", "gjp_texture.cu")]
 LIB = os.path.join(HERE, "libgjp.so")
+# debug build: every tap of the unchecked interior marches range-checked (GJP_CHECK_TAPS)
+LIB_CHECKED = os.path.join(HERE, "libgjp_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -24,21 +26,21 @@ def nvcc() -> str:
     return cand
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = SOURCES + [os.path.join(INCLUDE, "gjp.h")] + [
         os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+def build(force: bool = False, verbose: bool = False, extra=None, lib: str = LIB) -> str:
     """Compiles every translation unit in parallel (one nvcc each), then
-    links the shared library; returns its path."""
-    if not force and not stale():
-        return LIB
-    tag = f".{os.getpid()}.tmp"   # objects: <name>.<pid>.tmp.o (nvcc dispatches on the suffix)
+    links the shared library `lib`; returns its path."""
+    if not force and not stale(lib):
+        return lib
+    tag = f".{os.path.basename(lib)}.{os.getpid()}.tmp"   # objects: <name>.<lib>.<pid>.tmp.o (nvcc reads the suffix)
     flags = [*(extra or []), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
     if verbose:
         flags.insert(0, "-Xptxas=-v")
@@ -49,14 +51,19 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
         for src, code in zip(SOURCES, codes):
             if code != 0:
                 raise subprocess.CalledProcessError(code, f"nvcc -c {src}")
-        tmp = LIB + tag
+        tmp = lib + tag
         subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     finally:
         for obj in objs:
             if os.path.exists(obj):
                 os.unlink(obj)
-    return LIB
+    return lib
+
+
+def build_checked(force: bool = False) -> str:
+    """The debug library: the same sources with GJP_CHECK_TAPS=1."""
+    return build(force=force, extra=["-DGJP_CHECK_TAPS=1"], lib=LIB_CHECKED)
 
 
 if __name__ == "__main__":

@@ -229,6 +229,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // barrier expects one arrival and none comes).  The wait gives up after its
 // limit, sets the status word and the kernel returns; no memory other than
 // its own shared word is touched.
+// Debug build: one thread records a tap outside the grid through the same
+// check as the marches (indices only; nothing is accessed).
+__global__ void gjp_tap_check_selftest_kernel() { taps_in_grid(-1, 0, 0, 1, 2, 2); }
+
 __global__ void gjp_wait_selftest_kernel()
 {
     __shared__ unsigned long long bar;
@@ -507,11 +511,12 @@ __device__ __forceinline__ float march_interior_pf(const T *__restrict__ vol, co
         for (int t = 0; t < kBatch; ++t) {
             da[t] = frac_of(pa);
             db[t] = frac_of(pb);
+            const bool ok = taps_in_grid(i + t, floor_of(pa), floor_of(pb), R.nm, R.na, R.nb);   // debug build only
             const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-            v00[t] = load_voxel(p);
-            v01[t] = load_voxel(p + sb);
-            v10[t] = load_voxel(p + sa);
-            v11[t] = load_voxel(p + sa + sb);
+            v00[t] = ok ? load_voxel(p) : 0.0f;
+            v01[t] = ok ? load_voxel(p + sb) : 0.0f;
+            v10[t] = ok ? load_voxel(p + sa) : 0.0f;
+            v11[t] = ok ? load_voxel(p + sa + sb) : 0.0f;
             pa += ga;
             pb += gb;
             plane += sm;
@@ -533,9 +538,10 @@ __device__ __forceinline__ float march_interior_pf(const T *__restrict__ vol, co
     acc += part;
     for (; i <= R.j_hi; ++i) {
         const float da = frac_of(pa), db = frac_of(pb);
+        const bool ok = taps_in_grid(i, floor_of(pa), floor_of(pb), R.nm, R.na, R.nb);
         const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-        const float v00 = load_voxel(p), v01 = load_voxel(p + sb);
-        const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + sb);
+        const float v00 = ok ? load_voxel(p) : 0.0f, v01 = ok ? load_voxel(p + sb) : 0.0f;
+        const float v10 = ok ? load_voxel(p + sa) : 0.0f, v11 = ok ? load_voxel(p + sa + sb) : 0.0f;
         const float e0 = __fmaf_rn(db, v01 - v00, v00);
         const float e1 = __fmaf_rn(db, v11 - v10, v10);
         acc += __fmaf_rn(da, e1 - e0, e0);
@@ -585,10 +591,12 @@ __device__ __forceinline__ void scatter_ray(const Ray &R, float ys, float *__res
         const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
         float *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
         const float w0 = (1.0f - da) * ys, w1 = da * ys;
-        atomicAdd(p, w0 * (1.0f - db));
-        atomicAdd(p + sb, w0 * db);
-        atomicAdd(p + sa, w1 * (1.0f - db));
-        atomicAdd(p + sa + sb, w1 * db);
+        if (taps_in_grid(i, floor_of(pa), floor_of(pb), R.nm, R.na, R.nb)) {   // always true but in the debug build
+            atomicAdd(p, w0 * (1.0f - db));
+            atomicAdd(p + sb, w0 * db);
+            atomicAdd(p + sa, w1 * (1.0f - db));
+            atomicAdd(p + sa + sb, w1 * db);
+        }
         pa += (unsigned long long)R.Ga;
         pb += (unsigned long long)R.Gb;
         plane += sm;
@@ -741,8 +749,9 @@ __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, uns
         red_add_if(z1 && w1 && r0, p + 1, wa0 * x1);
         red_add_if(z1 && w1 && r1, p + sa + 1, da * x1);
     } else {
-        red_add2_if(w0, p, wa0 * x0, p + sa, da * x0);
-        red_add2_if(w1, p + 1, wa0 * x1, p + sa + 1, da * x1);
+        const bool ok = taps_in_grid(i, ia, ib, R.nm, R.na, R.nb);   // always true but in the debug build
+        red_add2_if(ok && w0, p, wa0 * x0, p + sa, da * x0);
+        red_add2_if(ok && w1, p + 1, wa0 * x1, p + sa + 1, da * x1);
     }
     pa += (unsigned long long)R.Ga;
     pb += (unsigned long long)R.Gb;
@@ -753,8 +762,10 @@ __device__ __forceinline__ void combine_plane(const Ray &R, int i, float yw, uns
 // row table (entry weight bits, offset).
 template <bool SPL, bool RUNS, bool ASC>
 __device__ __forceinline__ void combine_row_plane(float yw, unsigned wbits, unsigned off, unsigned long long &pb,
-                                                  unsigned long long gb, int sa, float *__restrict__ vol)
+                                                  unsigned long long gb, int sa, float *__restrict__ vol, int i,
+                                                  const Ray &R)
 {
+    // (i: the plane, for the tap check of the debug build)
     const int ib = floor_of(pb);
     const float db = upper_weight<SPL>(frac_of(pb));
     const float g1 = yw * db;
@@ -764,8 +775,9 @@ __device__ __forceinline__ void combine_row_plane(float yw, unsigned wbits, unsi
     combine_lane<RUNS, ASC>(ib, g0, g1, x0, x1, w0, w1);
     float *p = vol + (int)(off + (unsigned)ib);
     const float da = __uint_as_float(wbits), wa0 = 1.0f - da;
-    red_add2_if(w0, p, wa0 * x0, p + sa, da * x0);
-    red_add2_if(w1, p + 1, wa0 * x1, p + sa + 1, da * x1);
+    const bool ok = row_taps_in_grid(off, i, ib, R);   // always true but in the debug build
+    red_add2_if(ok && w0, p, wa0 * x0, p + sa, da * x0);
+    red_add2_if(ok && w1, p + 1, wa0 * x1, p + sa + 1, da * x1);
     pb += gb;
 }
 
@@ -795,12 +807,12 @@ __device__ __forceinline__ void combine_rows(const Ray &R, int i_lo, int i_hi, f
         int j = 0;
         for (; j + 1 < n; j += 2) {
             const uint4 e = *reinterpret_cast<const uint4 *>(rows + j);
-            combine_row_plane<SPL, RUNS, ASC>(yw, e.x, e.y, pb, gb, sa, vol);
-            combine_row_plane<SPL, RUNS, ASC>(yw, e.z, e.w, pb, gb, sa, vol);
+            combine_row_plane<SPL, RUNS, ASC>(yw, e.x, e.y, pb, gb, sa, vol, w + j, R);
+            combine_row_plane<SPL, RUNS, ASC>(yw, e.z, e.w, pb, gb, sa, vol, w + j + 1, R);
         }
         if (j < n) {
             const uint2 e = rows[j];
-            combine_row_plane<SPL, RUNS, ASC>(yw, e.x, e.y, pb, gb, sa, vol);
+            combine_row_plane<SPL, RUNS, ASC>(yw, e.x, e.y, pb, gb, sa, vol, w + j, R);
         }
     }
 }
@@ -1794,9 +1806,20 @@ gjp_status gjp_selftest_wait_timeout(void *stream)
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
+gjp_status gjp_selftest_tap_check(void *stream)
+{
+    if (!GJP_CHECK_TAPS) return GJP_ERR_UNSUPPORTED;
+    gjp_tap_check_selftest_kernel<<<1, 1, 0, (cudaStream_t)stream>>>();
+    return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+}
+
 gjp_status gjp_stream_status(void *stream)
 {
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GJP_ERR_CUDA;
+    if (GJP_CHECK_TAPS) {
+        const unsigned taps = take_tap_faults() | batch_tap_faults() | texture_tap_faults();
+        if (taps) return GJP_ERR_INTERNAL;
+    }
     unsigned flag = 0;
     if (cudaMemcpyFromSymbol(&flag, g_gjp_status, sizeof flag) != cudaSuccess) return GJP_ERR_CUDA;
     if (flag) {

@@ -157,6 +157,8 @@ BatchKernel batch_kernel(bool any_i64, bool any_spl)
 }
 
 }  // namespace
+unsigned batch_tap_faults() { return take_tap_faults(); }
+
 }  // namespace gjp_detail
 
 using namespace gjp_detail;

@@ -65,6 +65,15 @@ struct VolParams {
 #ifndef GJP_ROWS
 #define GJP_ROWS 1
 #endif
+// Debug build: GJP_CHECK_TAPS=1 range-checks every tap that the interior
+// marches read or reduce without a per-tap test (their plane ranges come
+// from the trimmed estimate of plane_interval).  A tap outside the grid is
+// skipped and recorded in a device status word instead of being accessed;
+// gjp_stream_status then reports GJP_ERR_INTERNAL.  Off by default: the
+// production kernels carry no check.
+#ifndef GJP_CHECK_TAPS
+#define GJP_CHECK_TAPS 0
+#endif
 constexpr int kTileV = 32;          // lanes of a warp along v (contiguous z)
 constexpr int kTileU = GJP_TILE_U;  // default warps of a block along u
 #ifndef GJP_MAX_TILE_U
@@ -74,6 +83,9 @@ constexpr int kMaxTileU = GJP_MAX_TILE_U;   // largest block: 8 warps
 constexpr int kMaxThreads = kTileV * kMaxTileU;
 constexpr int kBatch = GJP_BATCH;   // interior planes per batch
 static_assert(kBatch % 2 == 0, "interior batches are evaluated two planes at a time");
+// the row-table march reads its 32-entry per-warp table in blocks of 4
+// batches = 16 planes; other batch sizes would index past the table
+static_assert(4 * kBatch == 16, "the row-table march is written for 4-plane batches");
 // register budget of the one-thread-per-ray kernels: the same per-thread
 // limit as GJP_MIN_BLOCKS resident blocks of 4 warps
 constexpr int kMinBlocksMax = (GJP_MIN_BLOCKS * 4 + kMaxTileU - 1) / kMaxTileU;
@@ -131,6 +143,10 @@ size_t elem_size(gjp_dtype t);
 gjp_status forward_texture(const void *d_volume, gjp_dtype dt, const int64_t n[3], const VolParams &V,
                            const gjp_geometry &g, gjp_cache_entry &entry, float *proj, int path, cudaStream_t s);
 void free_texture_cache(gjp_cache_entry &e);
+// Tap-check faults recorded by the kernels of the other translation units
+// (debug build; 0 otherwise), read and cleared.
+unsigned batch_tap_faults();
+unsigned texture_tap_faults();
 
 // ---------------------------------------------------------------------------
 // Device side: double-float helpers (error-free transformations with FMA).
@@ -308,6 +324,7 @@ __device__ __forceinline__ float2 eq12_pair(typename Raw<T>::type v00x, typename
 
 struct Ray {
     int m, na, nb;            // driving axis (Eq. 3) and transverse extents
+    int nm;                   // extent along m
     long long sm, sa, sb;     // element strides of m, a, b
     long long Pa, Pb;         // transverse positions at plane ic, fixed 32.32
     long long Ga, Gb;         // increments per plane (rt_a, rt_b of Eq. 4), fixed 32.32
@@ -316,6 +333,50 @@ struct Ray {
     int j_lo, j_hi;           // interior planes: all four taps inside the grid
     float step;               // |h (.) rt|: world length of one plane step
 };
+
+// ---------------------------------------------------------------------------
+// Tap check of the debug build (GJP_CHECK_TAPS).  One status word per
+// translation unit; take_tap_faults() reads and clears this unit's word.
+
+static __device__ unsigned g_gjp_tap_fault;
+
+// Whether the four taps of a sample with lower corner (ia, ib) on plane i lie
+// in the grid (i in [0, nm), ia + 1 < na, ib + 1 < nb); records a violation.
+// Always true, and free, in the production build.
+__device__ __forceinline__ bool taps_in_grid(int i, int ia, int ib, int nm, int na, int nb)
+{
+    if (!GJP_CHECK_TAPS) return true;
+    const bool ok = (unsigned)i < (unsigned)nm && ia >= 0 && ia + 1 < na && ib >= 0 && ib + 1 < nb;
+    if (!ok) atomicOr(&g_gjp_tap_fault, 1u);
+    return ok;
+}
+
+// The same for a row-table entry: `off` = i sm + ia sa (32-bit offsets) of
+// plane i, z index ib.
+__device__ __forceinline__ bool row_taps_in_grid(unsigned off, int i, int ib, const Ray &R)
+{
+    if (!GJP_CHECK_TAPS) return true;
+    const unsigned rel = off - (unsigned)i * (unsigned)R.sm;
+    const bool whole = rel % (unsigned)R.sa == 0u;
+    const bool ok = whole && taps_in_grid(i, (int)(rel / (unsigned)R.sa), ib, R.nm, R.na, R.nb);
+    if (!whole) atomicOr(&g_gjp_tap_fault, 1u);
+    return ok;
+}
+
+static inline unsigned take_tap_faults()
+{
+#if GJP_CHECK_TAPS
+    unsigned f = 0;
+    if (cudaMemcpyFromSymbol(&f, g_gjp_tap_fault, sizeof f) != cudaSuccess) return 0;
+    if (f) {
+        const unsigned z = 0;
+        cudaMemcpyToSymbol(g_gjp_tap_fault, &z, sizeof z);
+    }
+    return f;
+#else
+    return 0;
+#endif
+}
 
 __device__ __forceinline__ long long pos_at(long long P, long long G, int i, int ic)
 {
@@ -420,6 +481,7 @@ __device__ __forceinline__ void setup_ray(const ViewParams &vp, const VolParams 
 
     const int nm = sel3(V.n[0], V.n[1], V.n[2], m);
     R.m = m;
+    R.nm = nm;
     R.na = sel3(V.n[0], V.n[1], V.n[2], a);
     R.nb = sel3(V.n[0], V.n[1], V.n[2], b);
     R.sm = sel3(V.s[0], V.s[1], V.s[2], m);
@@ -512,7 +574,8 @@ __device__ __forceinline__ void block_tile_view(int n_views, int view_group, int
 template <typename T, typename Index, bool SPL>
 __device__ __forceinline__ float2 interior_batch(const T *__restrict__ vol, unsigned long long &pa,
                                                  unsigned long long &pb, Index &plane, unsigned long long ga,
-                                                 unsigned long long gb, Index sa, Index sb, Index sm)
+                                                 unsigned long long gb, Index sa, Index sb, Index sm, int &ii,
+                                                 int di, const Ray &R)
 {
     using W = typename Raw<T>::type;
     W v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch];
@@ -521,14 +584,16 @@ __device__ __forceinline__ float2 interior_batch(const T *__restrict__ vol, unsi
     for (int t = 0; t < kBatch; ++t) {
         qa[t] = pa;
         qb[t] = pb;
+        const bool ok = taps_in_grid(ii, floor_of(pa), floor_of(pb), R.nm, R.na, R.nb);   // debug build only
         const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-        v00[t] = load_raw(p);
-        v01[t] = load_raw(p + sb);
-        v10[t] = load_raw(p + sa);
-        v11[t] = load_raw(p + sa + sb);
+        v00[t] = ok ? load_raw(p) : W(0);
+        v01[t] = ok ? load_raw(p + sb) : W(0);
+        v10[t] = ok ? load_raw(p + sa) : W(0);
+        v11[t] = ok ? load_raw(p + sa + sb) : W(0);
         pa += ga;
         pb += gb;
         plane += sm;
+        ii += di;
     }
     float2 bsum = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -558,6 +623,8 @@ __device__ __forceinline__ float march_interior(const T *__restrict__ vol, const
     const unsigned long long gb = rev ? 0ull - (unsigned long long)R.Gb : (unsigned long long)R.Gb;
     const Index sm = rev ? -(Index)R.sm : (Index)R.sm;
     Index plane = (Index)i0 * (Index)R.sm;
+    int ii = i0;                                     // plane index (checked in the debug build)
+    const int di = rev ? -1 : 1;
     // two-level sum: planes of a batch are added together, four batch sums
     // make a block sum, and block sums join the total once per 16 planes
     // (float32 error ~4x smaller than a running sum over up to ~n_m planes);
@@ -567,25 +634,27 @@ __device__ __forceinline__ float march_interior(const T *__restrict__ vol, const
         float2 blk = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            blk = __fadd2_rn(blk, interior_batch<T, Index, SPL>(vol, pa, pb, plane, ga, gb, sa, sb, sm));
+            blk = __fadd2_rn(blk, interior_batch<T, Index, SPL>(vol, pa, pb, plane, ga, gb, sa, sb, sm, ii, di, R));
         acc = __fadd2_rn(acc, blk);
     }
     float2 part = make_float2(0.0f, 0.0f);           // fewer than 16 planes left
     for (; count >= kBatch; count -= kBatch)
-        part = __fadd2_rn(part, interior_batch<T, Index, SPL>(vol, pa, pb, plane, ga, gb, sa, sb, sm));
+        part = __fadd2_rn(part, interior_batch<T, Index, SPL>(vol, pa, pb, plane, ga, gb, sa, sb, sm, ii, di, R));
     acc = __fadd2_rn(acc, part);
     float tail = 0.0f;
     for (; count > 0; --count) {
         const float da = upper_weight<SPL>(frac_of(pa)), db = upper_weight<SPL>(frac_of(pb));
+        const bool ok = taps_in_grid(ii, floor_of(pa), floor_of(pb), R.nm, R.na, R.nb);
         const T *p = vol + (plane + (Index)floor_of(pa) * sa + (Index)floor_of(pb) * sb);
-        const float v00 = load_voxel(p), v01 = load_voxel(p + sb);
-        const float v10 = load_voxel(p + sa), v11 = load_voxel(p + sa + sb);
+        const float v00 = ok ? load_voxel(p) : 0.0f, v01 = ok ? load_voxel(p + sb) : 0.0f;
+        const float v10 = ok ? load_voxel(p + sa) : 0.0f, v11 = ok ? load_voxel(p + sa + sb) : 0.0f;
         const float e0 = __fmaf_rn(db, v01 - v00, v00);
         const float e1 = __fmaf_rn(db, v11 - v10, v10);
         tail += __fmaf_rn(da, e1 - e0, e0);
         pa += ga;
         pb += gb;
         plane += sm;
+        ii += di;
     }
     return (acc.x + acc.y) + tail;
 }
@@ -628,8 +697,10 @@ __device__ __forceinline__ float march_boundary(const T *__restrict__ vol, const
 template <typename T, bool SPL, bool CHECKED>
 __device__ __forceinline__ float2 rows_block(const T *__restrict__ vol, const uint4 *__restrict__ e,
                                              unsigned long long &pb, unsigned long long gb, int sa, int d, int cnt,
-                                             int n)
+                                             int n, int ip, int dir, const Ray &R)
 {
+    // (ip, dir: plane index of entry 0 and the march direction, for the
+    // tap check of the debug build)
     using W = typename Raw<T>::type;
     float2 blk = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -650,17 +721,20 @@ __device__ __forceinline__ float2 rows_block(const T *__restrict__ vol, const ui
         for (int t = 0; t < kBatch; ++t) {
             qb[t] = pb;
             const T *p = vol + (int)(off[t] + (unsigned)floor_of(pb));
+            const int i = ip + dir * (q * kBatch + t);
             if (CHECKED) {
-                const bool in = (unsigned)(d + q * kBatch + t) < (unsigned)cnt;
+                const bool in = (unsigned)(d + q * kBatch + t) < (unsigned)cnt &&
+                                (!GJP_CHECK_TAPS || row_taps_in_grid(off[t], i, floor_of(pb), R));
                 v00[t] = in ? load_raw(p) : W(0);
                 v01[t] = in ? load_raw(p + 1) : W(0);
                 v10[t] = in ? load_raw(p + sa) : W(0);
                 v11[t] = in ? load_raw(p + sa + 1) : W(0);
             } else {
-                v00[t] = load_raw(p);
-                v01[t] = load_raw(p + 1);
-                v10[t] = load_raw(p + sa);
-                v11[t] = load_raw(p + sa + 1);
+                const bool ok = row_taps_in_grid(off[t], i, floor_of(pb), R);   // debug build only
+                v00[t] = ok ? load_raw(p) : W(0);
+                v01[t] = ok ? load_raw(p + 1) : W(0);
+                v10[t] = ok ? load_raw(p + sa) : W(0);
+                v11[t] = ok ? load_raw(p + sa + 1) : W(0);
             }
             pb += gb;
         }
@@ -727,10 +801,12 @@ __device__ __forceinline__ float march_interior_rows(const T *__restrict__ vol, 
         const int nw = min(32, L - w);
         for (int kb = 0; kb < nw; kb += 16) {
             const int k = w + kb;
+            const int ip = i0 + dir * k;
             if (k >= K0 && k + 15 <= K1)              // warp-uniform
-                acc = __fadd2_rn(acc, rows_block<T, SPL, false>(vol, rows + kb / 2, pb, gb, sa, 0, 0, 16));
+                acc = __fadd2_rn(acc, rows_block<T, SPL, false>(vol, rows + kb / 2, pb, gb, sa, 0, 0, 16, ip, dir, R));
             else
-                acc = __fadd2_rn(acc, rows_block<T, SPL, true>(vol, rows + kb / 2, pb, gb, sa, k - k_lo, cnt, L - k));
+                acc = __fadd2_rn(acc, rows_block<T, SPL, true>(vol, rows + kb / 2, pb, gb, sa, k - k_lo, cnt, L - k,
+                                                               ip, dir, R));
         }
     }
     return acc.x + acc.y;

@@ -388,4 +388,6 @@ gjp_status forward_texture(const void *d_volume, gjp_dtype dt, const int64_t n[3
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
+unsigned texture_tap_faults() { return take_tap_faults(); }
+
 }  // namespace gjp_detail
