@@ -16,10 +16,18 @@ whole step; per-kernel rates, bytes and roofline fractions are reported
 alongside.  All inputs (512 MiB volume, 377 MB projections) are larger
 than the 129 MB L2, so no L2 flush is inserted between iterations.
 
+With the seeded random field as the timed content, the same three kernels
+are also timed on the 512^3 Shepp-Logan-shaped phantom (the other content
+of the workload), reported under ``kernels_phantom``.
+
     python bench.py [--steps K] [--warmup W] [--impl reference]
-    torchrun --nproc-per-node N bench.py --gpus N     (weak scaling: every
-        rank projects its own copy of the workload; no collective on the
-        data path)
+    torchrun --nproc-per-node N bench.py --gpus N     (one scan split by
+        views: every rank projects its range of the 360 views from its own
+        copy of the volume; the adjoint volumes are summed with one
+        all-reduce; total work is fixed, so scaling is strong)
+    python bench.py --ncu-summary counters.csv        (writes the committed
+        ncu counter record profiles/ncu_counters.json from an ncu --csv
+        metrics log of the first 16 views)
 """
 from __future__ import annotations
 
@@ -53,6 +61,9 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["gjp", "reference"], default="gjp")
     p.add_argument("--workload", choices=["step", "batch"], default="step",
                    help="step: the 512^3 hot-path step (default); batch: the 16-problem batching workload")
+    p.add_argument("--batch-mix", choices=["c5", "small"], default="c5",
+                   help="problems of --workload batch: the 16-problem c5 mix or 64 small problems")
+    p.add_argument("--no-batch", action="store_true", help="skip the small-problem batching figures of the step")
     p.add_argument("--n", type=int, default=512, help="volume edge (workload is defined at 512)")
     p.add_argument("--views", type=int, default=360)
     p.add_argument("--first-views", type=int, default=0,
@@ -64,7 +75,13 @@ def parse_args(argv=None):
     p.add_argument("--content", choices=["random", "phantom"], default="random")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU baseline sample")
+    p.add_argument("--no-phantom", action="store_true", help="skip the Shepp-Logan-shaped phantom timings")
+    p.add_argument("--oracle-blocks", type=int, default=3,
+                   help="CPU baseline sample: blocks of ORACLE_BLOCK evenly spaced views")
+    p.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
+    p.add_argument("--ncu-summary", default=None, help="ncu --csv metrics log to turn into profiles/ncu_counters.json")
+    p.add_argument("--ncu-views", type=int, default=16, help="views of the workload the ncu capture covered")
+    p.add_argument("--ncu-command", default="", help="the command line that made the ncu capture")
     return p.parse_args(argv)
 
 
@@ -239,10 +256,94 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def dram_traffic(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
-    None if absent or taken on different kernel sources."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+COUNTERS = os.path.join("profiles", "ncu_counters.json")
+# the kernel each step entry runs (ncu kernel-name prefix)
+KERNEL_NAMES = {"forward_f32": "gjp_forward_kernel<float", "forward_bf16": "gjp_forward_kernel<__nv_bfloat16",
+                "forward_f16": "gjp_forward_tld4_kernel<__half", "adjoint_f32": "gjp_adjoint_combine_kernel<int"}
+# ncu metric -> record field
+NCU_FIELDS = {
+    "gpu__time_duration.sum": "duration_ns",
+    "dram__bytes_read.sum": "dram_read_bytes",
+    "dram__bytes_write.sum": "dram_write_bytes",
+    "smsp__inst_executed.sum": "warp_instructions",
+    "l1tex__data_pipe_lsu_wavefronts.sum": "l1_wavefronts",
+    "lts__t_sectors_srcunit_tex_op_red.sum": "l2_red_sectors",
+    "smsp__inst_executed_op_global_red.sum": "red_instructions",
+    "smsp__issue_active.avg.pct_of_peak_sustained_elapsed": "issue_pct",
+    "l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed": "l1_wavefronts_pct",
+    "lts__t_sectors_srcunit_tex_op_red.avg.pct_of_peak_sustained_elapsed": "l2_red_pct",
+    "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_elapsed": "alu_pct",
+    "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_elapsed": "fma_pct",
+    "l1tex__t_sector_hit_rate.pct": "l1_hit_pct",
+    "lts__t_sector_hit_rate.pct": "l2_hit_pct",
+    "sm__warps_active.avg.pct_of_peak_sustained_active": "warps_active_pct",
+}
+_UNIT_SCALE = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12,
+               "ns": 1.0, "us": 1e3, "usecond": 1e3, "msecond": 1e6, "ms": 1e6, "nsecond": 1.0, "second": 1e9}
+# The binding unit of each kernel and the fewest of its operations per warp-plane (32
+# samples of one detector column) that the sample's tap pattern needs: every warp-plane
+# touches two transverse rows over the z-span of 32 neighbouring rays, 33 voxels
+# (132 bytes in float32: two 128-byte L1 lines and five 32-byte sectors; 66 bytes in
+# 16-bit storage: one or two lines, 1.5 on average).
+LIMIT_MODEL = {
+    "gjp_forward_kernel<float": ("l1_wavefronts", "l1_wavefronts_pct", "L1 data-pipe wavefronts", 2 * 2.0),
+    "gjp_forward_kernel<__nv_bfloat16": ("l1_wavefronts", "l1_wavefronts_pct", "L1 data-pipe wavefronts",
+                                         2 * 1.5),
+    "gjp_adjoint_combine_kernel<int": ("l2_red_sectors", "l2_red_pct", "L2 reduction sectors", 2 * 5.0),
+}
+
+
+def kernel_key(name: str) -> str:
+    """``gjp_forward_kernel<float`` from an ncu kernel name such as
+    ``void gjp_detail::gjp_forward_kernel<float, int, 0>(const T1 *, ...)``."""
+    import re
+    m = re.search(r"(\w+<[^,>(]+)", name.split("(")[0].replace("void ", ""))
+    return m.group(1) if m else name
+
+
+def _sources_hash():
+    out = {}
+    for rel in ("paper_1609_00958_gb300/csrc/gjp.cu", "paper_1609_00958_gb300/csrc/gjp_common.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            out[rel] = hashlib.sha256(f.read()).hexdigest()
+    return out
+
+
+def ncu_summary(csv_path: str, views: int, command: str, n: int = 512, n_views: int = 360) -> dict:
+    """The counter record of one ncu ``--metrics ... --csv`` log that covered
+    the first ``views`` views (one view group) of the workload: per kernel
+    the raw counters, DRAM bytes scaled to a full launch, and the samples the
+    capture processed.  Written to profiles/ncu_counters.json."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    head = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    hdr = rows[head]
+    ki, mi, ui, vi = (hdr.index(c) for c in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value"))
+    kernels = {}
+    for r in rows[head + 1:]:
+        if len(r) <= vi or r[mi] not in NCU_FIELDS:
+            continue
+        key = kernel_key(r[ki])
+        val = float(r[vi].replace(",", ""))
+        val *= _UNIT_SCALE.get(r[ui].strip().lower(), 1.0)
+        kernels.setdefault(key, {})[NCU_FIELDS[r[mi]]] = val   # the last launch of a kernel wins
+    vg, cg = synth.scaled_c2_geometry(n, n, n_views, 10.0)
+    samples = int(sample_counts(vg, cg.subset(range(views))).sum())
+    for e in kernels.values():
+        if "dram_read_bytes" in e and "dram_write_bytes" in e:
+            e["dram_bytes"] = e["dram_read_bytes"] + e["dram_write_bytes"]
+            e["bytes_per_launch"] = e["dram_bytes"] * n_views / views
+        e["samples_captured"] = samples
+    return {"sources": _sources_hash(), "kernels": kernels,
+            "capture": {"views": views, "of_views": n_views, "volume": n, "command": command,
+                        "note": f"one ncu capture of the first {views} views (one view group) of the {n_views}-view "
+                                f"{n}^3 workload; DRAM bytes scaled x{n_views / views:g} to a full launch"}}
+
+
+def ncu_record(kernel: str):
+    """The committed ncu counters of `kernel`, or None if absent or taken on
+    different kernel sources."""
+    path = os.path.join(ROOT, COUNTERS)
     try:
         with open(path) as f:
             d = json.load(f)
@@ -250,9 +351,45 @@ def dram_traffic(kernel: str):
             with open(os.path.join(ROOT, rel), "rb") as f:
                 if hashlib.sha256(f.read()).hexdigest() != sha:
                     return None
-        e = d["kernels"].get(kernel)
-        return None if e is None else float(e["bytes_per_launch"])
+        return d["kernels"].get(kernel)
     except (OSError, KeyError, ValueError, TypeError):
+        return None
+
+
+def dram_traffic(kernel: str, views: int | None = None):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu record (a
+    launch over the workload's 360 views, or over `views` views), or None if
+    absent or taken on different kernel sources."""
+    e = ncu_record(kernel)
+    try:
+        if e is None:
+            return None
+        per = float(e["bytes_per_launch"])
+        if views is not None:
+            with open(os.path.join(ROOT, COUNTERS)) as f:
+                per *= views / float(json.load(f)["capture"]["of_views"])
+        return per
+    except (OSError, KeyError, TypeError, ValueError):
+        return None
+
+
+def limiter(kernel: str):
+    """The kernel's binding unit from the committed ncu counters: its
+    utilisation (percent of its peak over the kernel), operations per sample
+    and the fewest per sample that the tap pattern needs (LIMIT_MODEL)."""
+    e = ncu_record(kernel)
+    model = LIMIT_MODEL.get(kernel)
+    if e is None or model is None:
+        return None
+    field, pct_field, unit, min_per_warp_plane = model
+    try:
+        per_sample = e[field] / e["samples_captured"]
+        least = min_per_warp_plane / 32.0
+        return {"unit": unit, "pct_of_peak": round(e[pct_field], 2), "per_sample": round(per_sample, 4),
+                "min_per_sample": round(least, 4), "efficiency": round(least / per_sample, 3),
+                "issue_pct": round(e.get("issue_pct", float("nan")), 2),
+                "source": COUNTERS}
+    except (KeyError, TypeError, ZeroDivisionError):
         return None
 
 
@@ -283,6 +420,20 @@ def gpu_id_for_smi(local):
         return str(local)
 
 
+def kernel_entry(name, ms, samples, alg_bytes, hbm, peak_kind, kname):
+    """Per-kernel figures of one timed kernel."""
+    gbs = alg_bytes / (ms * 1e-3) / 1e9
+    e = {"ms": round(ms, 4), "gsamples_s": round(samples / (ms * 1e-3) / 1e9, 2),
+         "algorithmic_gb": round(alg_bytes / 1e9, 4), "achieved_gbs": round(gbs, 1),
+         "frac_of_" + peak_kind + "_hbm": round(gbs / hbm, 4),
+         "paper_logical_gbs": round(samples * (8 if "16" in name and "f32" not in name else 16)
+                                    / (ms * 1e-3) / 1e9, 1)}
+    lim = limiter(kname) if kname else None
+    if lim is not None:
+        e["limiter"] = lim
+    return e
+
+
 def run_gjp(args):
     import torch
     from paper_1609_00958_gb300 import build as libbuild
@@ -292,13 +443,16 @@ def run_gjp(args):
 
     rank, world, local = dist_setup(args)
     dev = torch.device("cuda", torch.cuda.current_device())
-    vg, cg, wname = workload(args)
-    geom = gjp.Geometry.from_cone(cg)
+    vg, cg_full, wname = workload(args)
+    # one scan split by views across the ranks (the whole scan at N = 1)
+    scan = gdist.ShardedScan(cg_full)
+    cg = scan.local_cone
+    geom = scan.geometry
     if args.tile_u is not None or args.view_group is not None:
         tu, vgp = geom.launch
         geom.set_launch(args.tile_u or tu, args.view_group or vgp)
 
-    vol_np = make_volume(args, vg, seed=rank)
+    vol_np = make_volume(args, vg, seed=0)
     vol32 = torch.from_numpy(vol_np).to(dev)
     # the texture unit has no bfloat16 format: the texture families store the 16-bit form as float16
     tex = args.forward_path in ("texture", "hwlin")
@@ -309,7 +463,7 @@ def run_gjp(args):
     back = torch.empty(vg.n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    counts = sample_counts(vg, cg)
+    counts = sample_counts(vg, cg)                     # this rank's views
     samples_per_kernel = int(counts.sum())
     foot = np.array(gjp.footprint_voxels(geom, vg.n, vg.h, device=dev), dtype=np.float64)
     proj_bytes = 4.0 * cg.n_views * cg.nu * cg.nv
@@ -319,26 +473,31 @@ def run_gjp(args):
         "adjoint_f32": 8.0 * foot.sum() + proj_bytes,    # read-modify-write of each touched voxel per view
     }
 
-    names = ["forward_f32", k16, "adjoint_f32"]
+    names = ["forward_f32", k16, "adjoint_f32"] + (["allreduce"] if world > 1 else [])
 
-    def step(ev=None):
+    def step(ev=None, v32=vol32, v16=vol16):
         if ev is not None:
             ev[0].record(stream)
-        gjp.forward(vol32, geom, vg.h, out=proj32, path=args.forward_path)
+        gjp.forward(v32, geom, vg.h, out=proj32, path=args.forward_path)
         if ev is not None:
             ev[1].record(stream)
-        gjp.forward(vol16, geom, vg.h, out=proj16, path=args.forward_path)
+        gjp.forward(v16, geom, vg.h, out=proj16, path=args.forward_path)
         if ev is not None:
             ev[2].record(stream)
         gjp.adjoint(proj32, geom, vg.n, vg.h, out=back)
         if ev is not None:
             ev[3].record(stream)
+        if world > 1:
+            gdist.all_reduce_sum_(back)                  # A^T y of the whole scan on every rank
+            if ev is not None:
+                ev[4].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    nev = len(names) + 1
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(args.steps)]
     gdist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(gpu_id_for_smi(local)) as clk:
@@ -355,56 +514,66 @@ def run_gjp(args):
     ms_per_step = total_ms / args.steps
     per_kernel_ms = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                      for i, n in enumerate(names)}
-    samples_per_step = 3 * samples_per_kernel
-    job_samples_per_step = gdist.sum_over_ranks(samples_per_step)     # every rank projects its own workload
+    # samples of the whole scan: every rank's views, three kernels each
+    job_samples_per_step = gdist.sum_over_ranks(3 * samples_per_kernel)
     value = job_samples_per_step / (ms_per_step * 1e-3) / 1e9
 
     hbm, peak_kind = peaks()
-    kernels = {}
-    for n in names:
-        ms = per_kernel_ms[n]
-        gbs = alg_bytes[n] / (ms * 1e-3) / 1e9
-        kernels[n] = {"ms": round(ms, 4), "gsamples_s": round(samples_per_kernel / (ms * 1e-3) / 1e9, 2),
-                      "algorithmic_gb": round(alg_bytes[n] / 1e9, 4), "achieved_gbs": round(gbs, 1),
-                      "frac_of_" + peak_kind + "_hbm": round(gbs / hbm, 4),
-                      "paper_logical_gbs": round(samples_per_kernel * (8 if "16" in n and "f32" not in n else 16)
-                                                 / (ms * 1e-3) / 1e9, 1)}
-    dominant = max(names, key=lambda n: per_kernel_ms[n])
-    kmap = {"forward_f32": "gjp_forward_kernel<float", "forward_bf16": "gjp_forward_kernel<__nv_bfloat16",
-            "forward_f16": "gjp_forward_tld4_kernel<__half",
-            "adjoint_f32": "gjp_adjoint_combine_kernel<int"}
-    traffic = dram_traffic(kmap[dominant])
+    kernels = {n: kernel_entry(n, per_kernel_ms[n], samples_per_kernel, alg_bytes[n], hbm, peak_kind,
+                               KERNEL_NAMES.get(n)) for n in names if n != "allreduce"}
+    if world > 1:
+        kernels["allreduce"] = {"ms": round(per_kernel_ms["allreduce"], 4),
+                                "bytes": int(back.numel() * 4), "what": "sum of the adjoint volumes over the ranks"}
+    projector = [n for n in names if n != "allreduce"]
+    dominant = max(projector, key=lambda n: per_kernel_ms[n])
+    kname = KERNEL_NAMES[dominant]
+    traffic = dram_traffic(kname, cg.n_views)
+    dmsec = per_kernel_ms[dominant] * 1e-3
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": kernels[dominant]["achieved_gbs"],
                 "peak": hbm, "peak_kind": peak_kind + " (copy, MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
                 else "fallback", "unit": "GB/s",
-                "frac": round(kernels[dominant]["achieved_gbs"] / hbm, 4), "traffic": traffic}
+                "frac": round(kernels[dominant]["achieved_gbs"] / hbm, 4),
+                "frac_algorithmic": round(kernels[dominant]["achieved_gbs"] / hbm, 4),
+                "frac_note": "algorithmic bytes: per view, every voxel with a non-zero tap once (adjoint: read "
+                             "and written), summed over the views; views issued together share the L2, so the "
+                             "DRAM traffic is far lower (dram_frac)",
+                "traffic": traffic,
+                "dram_frac": None if traffic is None else round(traffic / dmsec / 1e9 / hbm, 4),
+                "limiter": kernels[dominant].get("limiter")}
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step)
+        e2e = run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step, world)
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (weights/accumulation); volume storage f32 and bf16",
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+        "dtype": "f32 (weights/accumulation); volume storage f32 and bf16",
         "data": "synthetic (seeded uniform [0,1) random field)" if args.content == "random"
         else "synthetic (Shepp-Logan-shaped phantom, project-owned ellipsoids)",
-        "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg.n_views,
+        "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg_full.n_views,
                    "launch": {"tile_u": geom.launch[0], "view_group": geom.launch[1]},
                    "forward_path": args.forward_path,
                    "step": "forward f32 + forward bf16 + adjoint f32", "samples_per_kernel": samples_per_kernel,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "one GPU" if world == 1 else
+                   f"one scan split by views over {world} GPUs (rank views {scan.start}..{scan.stop - 1}), "
+                   "adjoint volumes summed by one all-reduce"},
         "kernels": kernels, "roofline": roofline, "clocks": clocks,
         "gpu_launches": 3 * args.steps,
         "e2e": e2e,
     }
+    if world == 1 and args.content == "random" and not args.no_phantom and not args.first_views:
+        result["kernels_phantom"] = phantom_kernels(args, gjp, geom, vg, cg, dev, stream, hbm, peak_kind, k16)
+    if world == 1 and not args.no_batch and not args.first_views:
+        name, make = BATCH_MIXES["small"]
+        ms, samples, tunings, _ = batch_measure(make(), args.warmup, max(1, min(args.steps, 10)), dev)
+        result["batching_small"] = {"workload": name, "samples": samples, **batch_summary(ms, samples)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample_views = list(range(0, cg.n_views, max(1, cg.n_views // 36)))
-        gpu_views = {v: (proj32[v].cpu().numpy(), proj16[v].cpu().numpy()) for v in sample_views}
-        result["cpu_baseline"] = cpu_baseline(args, vg, cg, vol_np, counts, budget_s=args.cpu_seconds,
-                                              gpu_views=gpu_views)
+        result["cpu_baseline"] = cpu_baseline(args, gjp, geom, vg, cg, vol_np, counts, proj32, proj16, dev)
         if "error_vs_oracle" in result["cpu_baseline"]:
-            result["error_vs_oracle"] = result["cpu_baseline"]["error_vs_oracle"]
+            result["error_vs_oracle"] = result["cpu_baseline"].pop("error_vs_oracle")
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -412,7 +581,42 @@ def run_gjp(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step):
+def phantom_kernels(args, gjp, geom, vg, cg, dev, stream, hbm, peak_kind, k16):
+    """The three kernels of the step on the 512^3 Shepp-Logan-shaped
+    phantom (2x2x2 supersampled), timed with CUDA events like the step
+    (min(steps, 5) repetitions after the warm-up)."""
+    import torch
+    vol = torch.from_numpy(synth.voxelize(vg, supersample=2)).to(dev)
+    v16 = vol.to(torch.float16 if k16 == "forward_f16" else torch.bfloat16)
+    p32 = torch.empty(cg.n_views, cg.nv, cg.nu, device=dev)
+    p16 = torch.empty_like(p32)
+    bk = torch.empty(vg.n, device=dev)
+    fns = {"forward_f32": lambda: gjp.forward(vol, geom, vg.h, out=p32, path=args.forward_path),
+           k16: lambda: gjp.forward(v16, geom, vg.h, out=p16, path=args.forward_path),
+           "adjoint_f32": lambda: gjp.adjoint(p32, geom, vg.n, vg.h, out=bk)}
+    counts = sample_counts(vg, cg)
+    foot = np.array(gjp.footprint_voxels(geom, vg.n, vg.h, device=dev), dtype=np.float64)
+    proj_bytes = 4.0 * cg.n_views * cg.nu * cg.nv
+    alg = {"forward_f32": 4.0 * foot.sum() + proj_bytes, k16: 2.0 * foot.sum() + proj_bytes,
+           "adjoint_f32": 8.0 * foot.sum() + proj_bytes}
+    out = {}
+    reps = max(1, min(args.steps, 5))
+    for name, fn in fns.items():
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = kernel_entry(name, a.elapsed_time(b) / reps, int(counts.sum()), alg[name], hbm, peak_kind, None)
+    out["content"] = "Shepp-Logan-shaped phantom (project-owned ellipsoids), 2x2x2 supersampled"
+    return out
+
+
+def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step, world=1):
     """Same step through the public API with host buffers.  Every step copies
     its inputs (float32 and bfloat16 volume) from pinned host memory to the
     GPU and its results (both projections and the adjoint volume) back to
@@ -422,7 +626,10 @@ def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step):
     input copy overlaps step k's kernels; with one event per tensor each
     kernel waits only for its own input and each result is copied out as
     soon as its kernel ends.  The timed region covers all steps, every copy
-    included, and ends when the last results are on the host."""
+    included, and ends when the last results are on the host.  With the
+    scan split over several GPUs, every rank copies the volume in and its
+    own views' projections out, sums the adjoint volumes with the all-reduce
+    and copies the whole adjoint out; the byte counts are the job's."""
     import torch
     from paper_1609_00958_gb300 import dist as gdist
     h_vol32 = torch.from_numpy(vol_np).pin_memory()
@@ -461,6 +668,8 @@ def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step):
             gjp.forward(v16, geom, vg.h, out=p16, stream=s_comp)
             ev["f16"][b].record(s_comp)
             gjp.adjoint(p32, geom, vg.n, vg.h, out=back, stream=s_comp)
+            if world > 1:
+                gdist.all_reduce_sum_(back)
             ev["adj"][b].record(s_comp)
         with torch.cuda.stream(s_out):         # results of step k back to the host, each when ready
             s_out.wait_event(ev["f32"][b])
@@ -480,8 +689,8 @@ def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step):
         step(k)
     torch.cuda.synchronize()                   # the host holds every step's results
     wall = gdist.max_over_ranks(time.perf_counter() - t0)
-    bi = h_vol32.numel() * 4 + h_vol16.numel() * 2
-    bo = (2 * int(np.prod(pshape)) + int(np.prod(vg.n))) * 4
+    bi = gdist.sum_over_ranks(h_vol32.numel() * 4 + h_vol16.numel() * 2)
+    bo = gdist.sum_over_ranks((2 * int(np.prod(pshape)) + int(np.prod(vg.n))) * 4)
     return {"value": round(job_samples_per_step / (wall / args.steps) / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
             "ms_per_step": round(1e3 * wall / args.steps, 3),
@@ -490,19 +699,70 @@ def run_e2e(args, gjp, geom, vg, cg, vol_np, dev, stream, job_samples_per_step):
 
 
 # --- CPU oracle (baseline leg and reference arm) ----------------------------------
+#
+# Both legs time the oracle the same way: blocks of ORACLE_BLOCK evenly spaced
+# views of the scan, each block in three calls -- forward of the float32
+# volume, forward of the bfloat16-stored values, adjoint -- after one warm-up
+# call.  The oracle's adjoint scatters into one private FP64 volume per thread
+# and sums them once per call, so a call over a block of views pays that cost
+# once per block; the adjoint figure includes it.
 
-def oracle_step(oracle, vg, cg, vol_np, vol_bf16w, view, threads, counts, keep=None):
-    """One view of the step on the oracle (forward f32, forward of the
-    bfloat16-stored values, adjoint); `keep` collects the two projections."""
-    sub = cg.subset([view])
-    t0 = time.perf_counter()
+ORACLE_BLOCK = 4
+
+
+def oracle_views(n_views: int, count: int) -> list:
+    """``count`` views evenly spaced over the scan (distinct, ascending)."""
+    count = max(1, min(count, n_views))
+    return sorted({int(round(i * n_views / count)) % n_views for i in range(count)})
+
+
+def oracle_threads():
+    return os.cpu_count() or 1
+
+
+def oracle_adjoint_bytes(vg, threads):
+    """Room for every thread's private FP64 volume, within a quarter of the
+    host's physical memory."""
+    need = threads * float(np.prod(vg.n)) * 8.0 + 1.0
+    try:
+        phys = float(os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES"))
+        return min(need, 0.25 * phys)
+    except (ValueError, OSError, AttributeError):
+        return need
+
+
+def oracle_block(oracle, vg, cg, vol_np, vol_bf16w, views, threads, counts, y=None):
+    """One block of views on the oracle: per kernel (seconds, samples) and
+    the results.  The adjoint takes ``y`` (the projections of these views;
+    the oracle's own float32-volume projections when None)."""
+    import time as _t
+    sub = cg.subset(views)
+    samples = int(sum(int(counts[v]) for v in views))
+    t0 = _t.perf_counter()
     p = oracle.forward(vol_np, vg, sub, threads=threads)
+    t1 = _t.perf_counter()
     p16 = oracle.forward(vol_bf16w, vg, sub, threads=threads)
-    oracle.adjoint(p, vg, sub, threads=threads, max_bytes=16e9)
-    dt = time.perf_counter() - t0
-    if keep is not None:
-        keep[view] = (p[0], p16[0])
-    return dt, 3 * int(counts[view])
+    t2 = _t.perf_counter()
+    yy = p if y is None else np.asarray(y, dtype=np.float64)
+    back = oracle.adjoint(yy, vg, sub, threads=threads, max_bytes=oracle_adjoint_bytes(vg, threads))
+    t3 = _t.perf_counter()
+    times = {"forward_f32": t1 - t0, "forward_bf16": t2 - t1, "adjoint_f32": t3 - t2}
+    return times, samples, (p, p16, back)
+
+
+def oracle_warmup(oracle, vg, cg, vol_np, threads):
+    """Loads the library, starts the thread pool and pages the volume in."""
+    oracle.forward(vol_np, vg, cg.subset([0]), threads=threads)
+
+
+def oracle_rates(times_list, samples_list):
+    """Per-kernel and whole-step rates over the timed blocks."""
+    out = {}
+    for k in ("forward_f32", "forward_bf16", "adjoint_f32"):
+        t = sum(tm[k] for tm in times_list)
+        out[k] = {"gsamples_s": round(sum(samples_list) / t / 1e9, 5), "seconds": round(t, 6)}
+    total_t = sum(sum(tm.values()) for tm in times_list)
+    return 3 * sum(samples_list) / total_t / 1e9, total_t, out
 
 
 def bf16_widened(vol_np):
@@ -512,95 +772,167 @@ def bf16_widened(vol_np):
     return torch.from_numpy(vol_np).to(torch.bfloat16).float().numpy()
 
 
-def cpu_baseline(args, vg, cg, vol_np, counts, budget_s, gpu_views=None):
-    """The oracle timed on the host cores over a time-bounded sample of
-    views.  With `gpu_views` (view -> (float32 projection, bfloat16
-    projection) from the timed GPU step), the same oracle projections also
-    give the GPU results' error on those views: max and RMS |gpu - oracle|
-    relative to the oracle maximum, against the float32 volume and, for
-    bfloat16 storage, also against the stored (rounded) values."""
+def _err(gpu, ref):
+    d = np.abs(np.asarray(gpu, np.float64) - ref)
+    m = max(float(np.abs(ref).max()), 1e-30)
+    return {"max_rel": float(f"{d.max() / m:.3e}"), "rms_rel": float(f"{np.sqrt(np.mean(d * d)) / m:.3e}")}
+
+
+def _worst(es):
+    return {"max_rel": max(e["max_rel"] for e in es),
+            "rms_rel": float(f"{np.sqrt(np.mean([e['rms_rel'] ** 2 for e in es])):.3e}")}
+
+
+def oracle_leg(args, vg, cg, vol_np, counts, blocks, warm_blocks, gpu=None):
+    """The oracle timed on the host cores: ``warm_blocks`` untimed blocks,
+    then ``blocks`` timed, each block of views in three oracle calls.  With
+    ``gpu`` (per block: GPU float32 and bfloat16 projections of the block's
+    views and the GPU adjoint of those float32 projections), also the GPU's
+    error against the oracle on those views; the oracle's adjoint then takes
+    the GPU projections as its input, like the GPU adjoint."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = oracle_threads()
     vol_w = bf16_widened(vol_np)
-    views = list(range(0, cg.n_views, max(1, cg.n_views // 36)))
-    t_tot, s_tot, used, kept = 0.0, 0, [], {}
-    for v in views:
-        dt, s = oracle_step(oracle, vg, cg, vol_np, vol_w, v, threads, counts, keep=kept)
-        t_tot += dt
-        s_tot += s
-        used.append(v)
-        if t_tot >= budget_s:
-            break
-    out = {"value": round(s_tot / t_tot / 1e9, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
-           "sample": f"FP64 oracle (OpenMP, {threads} threads) on {len(used)} of {cg.n_views} views "
-                     f"(views {used[0]}..{used[-1]} step {views[1] - views[0] if len(views) > 1 else 0}): "
-                     "forward f32 + forward bf16-stored + adjoint per view, same volume and geometry"}
-    if gpu_views:
-        def err(gpu, ref):
-            d = np.abs(np.asarray(gpu, np.float64) - ref)
-            m = max(float(np.abs(ref).max()), 1e-30)
-            return {"max_rel": float(f"{d.max() / m:.3e}"), "rms_rel": float(f"{np.sqrt(np.mean(d * d)) / m:.3e}")}
-        e32 = [err(gpu_views[v][0], kept[v][0]) for v in used]
-        e16 = [err(gpu_views[v][1], kept[v][0]) for v in used]
-        e16s = [err(gpu_views[v][1], kept[v][1]) for v in used]
-        worst = lambda es: {"max_rel": max(e["max_rel"] for e in es),
-                            "rms_rel": float(f"{np.sqrt(np.mean([e['rms_rel'] ** 2 for e in es])):.3e}")}
+    oracle_warmup(oracle, vg, cg, vol_np, threads)
+    for blk in warm_blocks:
+        oracle_block(oracle, vg, cg, vol_np, vol_w, blk, threads, counts)
+    times, samples, e32, e16, e16s, eadj = [], [], [], [], [], []
+    for bi, blk in enumerate(blocks):
+        y = None if gpu is None else gpu[bi][0]
+        tm, smp, (p, p16, back) = oracle_block(oracle, vg, cg, vol_np, vol_w, blk, threads, counts, y=y)
+        times.append(tm)
+        samples.append(smp)
+        if gpu is not None:
+            g32, g16, gback = gpu[bi]
+            for j in range(len(blk)):
+                e32.append(_err(g32[j], p[j]))
+                e16.append(_err(g16[j], p[j]))
+                e16s.append(_err(g16[j], p16[j]))
+            eadj.append(_err(gback, back))
+        del back
+    value, total_t, per_kernel = oracle_rates(times, samples)
+    out = {"value": value, "seconds": total_t, "kernels": per_kernel, "threads": threads}
+    if gpu is not None:
         out["error_vs_oracle"] = {
-            "views": used, "forward_f32": worst(e32), "forward_bf16": worst(e16),
-            "forward_bf16_vs_stored_values": worst(e16s),
-            "bounds": {"f32": 1e-5, "bf16": 5e-3, "bf16_vs_stored_values": 1e-5}}
+            "views": [v for blk in blocks for v in blk], "forward_f32": _worst(e32), "forward_bf16": _worst(e16),
+            "forward_bf16_vs_stored_values": _worst(e16s),
+            "adjoint_f32": _worst(eadj) | {"what": f"A^T y of each block of {ORACLE_BLOCK} views, y = the GPU "
+                                                   "projections; GPU against the FP64 oracle"},
+            "bounds": {"f32": 1e-5, "bf16": 5e-3, "bf16_vs_stored_values": 1e-5, "adjoint_f32": 1e-5}}
     return out
 
 
+def baseline_blocks(n_views, n_blocks):
+    """``n_blocks`` blocks of ORACLE_BLOCK views, each spread over the scan,
+    plus one further such block for the warm-up."""
+    views = oracle_views(n_views, ORACLE_BLOCK * (n_blocks + 1))
+    blocks = [views[i::n_blocks + 1][:ORACLE_BLOCK] for i in range(n_blocks + 1)]
+    return blocks[1:], blocks[:1]
+
+
+def cpu_baseline(args, gjp, geom, vg, cg, vol_np, counts, proj32, proj16, dev):
+    """The oracle on the host cores over ``--oracle-blocks`` blocks of
+    ORACLE_BLOCK views, after one warm-up block: the reference arm's
+    procedure, run in a fresh child process (no CUDA) so that both legs time
+    the oracle under the same conditions.  The GPU results for those views
+    (float32 and bfloat16 projections, the adjoint of each block's float32
+    projections) go to the child through files, which returns the oracle's
+    rates and the GPU's error against it."""
+    import shutil
+    import subprocess as sp
+    blocks, warm = baseline_blocks(cg.n_views, args.oracle_blocks)
+    tmp = tempfile.mkdtemp(prefix="gjp_oracle_leg_")
+    try:
+        for bi, blk in enumerate(blocks):
+            gsub = gjp.Geometry.from_cone(cg.subset(blk))
+            gback = gjp.adjoint(proj32[blk].contiguous(), gsub, vg.n, vg.h)
+            np.save(os.path.join(tmp, f"p32_{bi}.npy"), proj32[blk].cpu().numpy())
+            np.save(os.path.join(tmp, f"p16_{bi}.npy"), proj16[blk].cpu().numpy())
+            np.save(os.path.join(tmp, f"back_{bi}.npy"), gback.cpu().numpy())
+            gsub.close()
+            del gback
+        with open(os.path.join(tmp, "blocks.json"), "w") as f:
+            json.dump({"blocks": blocks, "warm": warm}, f)
+        env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-leg", tmp, "--n", str(args.n),
+               "--views", str(args.views), "--content", args.content]
+        if args.first_views:
+            cmd += ["--first-views", str(args.first_views)]
+        res = sp.run(cmd, env=env, capture_output=True, text=True, check=True)
+        leg = json.loads(res.stdout.strip().splitlines()[-1])
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    views = [v for blk in blocks for v in blk]
+    return {"value": round(leg["value"], 5), "unit": UNIT, "cores": leg["threads"], "kind": "oracle",
+            "sample": f"FP64 oracle (OpenMP, {leg['threads']} threads, fresh process) on {len(views)} of "
+                      f"{cg.n_views} views in {len(blocks)} blocks of {ORACLE_BLOCK} spread over the scan, after "
+                      "one warm-up block: per block one forward of the float32 volume, one of the bfloat16-stored "
+                      "values and one adjoint; the adjoint includes summing its per-thread private volumes once "
+                      "per block",
+            "seconds": round(leg["seconds"], 3), "kernels": leg["kernels"],
+            "error_vs_oracle": leg["error_vs_oracle"]}
+
+
+def run_oracle_leg(args):
+    """Child process of cpu_baseline: times the oracle on the blocks named
+    in ``--oracle-leg DIR`` and compares it with the GPU results there."""
+    vg, cg, _ = workload(args)
+    vol_np = make_volume(args, vg, seed=0)
+    counts = sample_counts(vg, cg)
+    with open(os.path.join(args.oracle_leg, "blocks.json")) as f:
+        spec = json.load(f)
+    gpu = [(np.load(os.path.join(args.oracle_leg, f"p32_{bi}.npy")),
+            np.load(os.path.join(args.oracle_leg, f"p16_{bi}.npy")),
+            np.load(os.path.join(args.oracle_leg, f"back_{bi}.npy"))) for bi in range(len(spec["blocks"]))]
+    out = oracle_leg(args, vg, cg, vol_np, counts, spec["blocks"], spec["warm"], gpu=gpu)
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, one block of
+    ORACLE_BLOCK views spread over the scan per step (forward float32,
+    forward of the bfloat16-stored values, adjoint), the procedure of the
+    GPU arm's cpu_baseline."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
     vg, cg, wname = workload(args)
     vol_np = make_volume(args, vg, seed=0)
-    vol_w = bf16_widened(vol_np)
     counts = sample_counts(vg, cg)
-    threads = os.cpu_count() or 1
-    stride = max(1, cg.n_views // max(1, args.steps + args.warmup))
-    order = [(k * stride) % cg.n_views for k in range(args.steps + args.warmup)]
-    for v in order[:args.warmup]:
-        oracle_step(oracle, vg, cg, vol_np, vol_w, v, threads, counts)
-    times, samples = [], 0
-    for v in order[args.warmup:]:
-        dt, s = oracle_step(oracle, vg, cg, vol_np, vol_w, v, threads, counts)
-        times.append(dt)
-        samples += s
-    total = sum(times)
-    value = samples / total / 1e9
-    sample = (f"one view per step (forward f32 + forward bf16-stored + adjoint), views {order[args.warmup:]}, "
-              f"FP64 oracle with {threads} OpenMP threads")
+    n_steps = args.steps + max(1, args.warmup)
+    views = oracle_views(cg.n_views, ORACLE_BLOCK * n_steps)
+    blocks = [views[i::n_steps][:ORACLE_BLOCK] for i in range(n_steps)]   # each block spans the scan
+    warm = blocks[:n_steps - args.steps]
+    leg = oracle_leg(args, vg, cg, vol_np, counts, blocks[len(warm):], warm)
+    value, total_t, threads = leg["value"], leg["seconds"], leg["threads"]
+    sample = (f"one block of {ORACLE_BLOCK} views per step (forward f32 + forward bf16-stored + adjoint, "
+              f"one oracle call each), {args.steps} blocks spread over the scan after {len(warm)} warm-up "
+              f"block(s), FP64 oracle with {threads} OpenMP threads; the adjoint includes summing its "
+              "per-thread private volumes once per block")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / max(1, len(times)), 3),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total_t / max(1, args.steps), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded uniform [0,1) random field)" if args.content == "random" else "synthetic phantom",
         "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg.n_views,
-                   "step": "one view: forward f32 + forward bf16 + adjoint (oracle)"},
+                   "step": f"one block of {ORACLE_BLOCK} views: forward f32 + forward bf16 + adjoint (oracle)"},
+        "kernels": leg["kernels"],
         "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def run_batch(args):
-    """The batching workload: 16 independent problems (synth.c5_manifest)
-    projected (a) by 16 separate gjp_forward launches, (b) by one persistent
-    batched launch with the geometries' default launch shapes, (c) the same
-    after gjp_batch_autotune, (d) (c) replayed from a CUDA graph.  One JSON
-    line; `value` is (d) in Gsamples/s."""
+def batch_measure(specs, warmup, steps, dev, clocks=False):
+    """Times one set of independent problems (synth BatchProblemSpec) five
+    ways, CUDA events over ``steps`` repetitions after ``warmup``:
+    separate gjp_forward launches on one stream, the same launches replayed
+    from a CUDA graph, one persistent batched launch with the geometries'
+    default launch shapes, the same after gjp_batch_autotune, and that
+    replayed from a CUDA graph.  Returns (ms per variant, samples, tunings,
+    clock record or None)."""
     import torch
-    from paper_1609_00958_gb300 import build as libbuild
-    libbuild.build()
     import paper_1609_00958_gb300 as gjp
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    specs = synth.c5_manifest()
     items, samples = [], 0
     for sp in specs:
         vg, cg = sp.geometry()
@@ -613,7 +945,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn, reps):
-        for _ in range(args.warmup):
+        for _ in range(max(1, warmup)):
             fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -628,39 +960,81 @@ def run_batch(args):
         for vol, g, h, origin, out in items:
             gjp.forward(vol, g, h, origin, out=out)
 
+    ms = {"separate_launches": timed(separate, steps)}
+    sep_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(sep_graph):
+        separate()
+    ms["separate_launches_graph"] = timed(sep_graph.replay, steps)
     batch = gjp.Batch(items)
-    ms_sep = timed(separate, args.steps)
-    ms_batch = timed(batch.forward, args.steps)
+    ms["batched"] = timed(batch.forward, steps)
     tunings = batch.autotune(reps=2)
-    ms_tuned = timed(batch.forward, args.steps)
+    ms["batched_autotuned"] = timed(batch.forward, steps)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         batch.forward()
-    with ClockSampler(gpu_id_for_smi(0)) as clk:
-        ms_graph = timed(graph.replay, args.steps)
-    clocks = clk.summary()
-    gsps = lambda ms: round(samples / (ms * 1e-3) / 1e9, 2)
+    clk = None
+    if clocks:
+        with ClockSampler(gpu_id_for_smi(0)) as c:
+            ms["batched_autotuned_graph"] = timed(graph.replay, steps)
+        clk = c.summary()
+    else:
+        ms["batched_autotuned_graph"] = timed(graph.replay, steps)
+    return {k: round(v, 3) for k, v in ms.items()}, samples, tunings, clk
+
+
+def batch_summary(ms, samples):
+    gsps = lambda m: round(samples / (m * 1e-3) / 1e9, 2)
+    return {"ms": ms, "gsamples_s": {k: gsps(v) for k, v in ms.items()},
+            "speedup_vs_separate": round(ms["separate_launches"] / ms["batched_autotuned_graph"], 3),
+            "speedup_vs_separate_graph": round(ms["separate_launches_graph"] / ms["batched_autotuned_graph"], 3)}
+
+
+BATCH_MIXES = {
+    "c5": ("batching form: 16 problems, 96^3..768^3 and 512x512x128, 90..720 views, 128^2..768^2 detectors, "
+           "5..15 deg half-angles (synth.c5_manifest)", lambda: synth.c5_manifest()),
+    "small": ("batching form, many small problems: 64 problems, 64^3..192^3, 16..96 views, 64^2..224^2 detectors, "
+              "5..15 deg half-angles (synth.small_batch_manifest)", lambda: synth.small_batch_manifest()),
+}
+
+
+def run_batch(args):
+    """The batching workload (``--batch-mix``): independent problems
+    projected by separate launches (plain and from a CUDA graph) and by one
+    persistent batched launch (default shapes, autotuned, autotuned from a
+    CUDA graph).  One JSON line; ``value`` is the autotuned batched launch
+    replayed from a CUDA graph, in Gsamples/s."""
+    import torch
+    from paper_1609_00958_gb300 import build as libbuild
+    libbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    name, make = BATCH_MIXES[args.batch_mix]
+    specs = make()
+    ms, samples, tunings, clocks = batch_measure(specs, args.warmup, args.steps, dev, clocks=True)
+    out = batch_summary(ms, samples)
     print(json.dumps({
-        "metric": METRIC + " (batching form)", "value": gsps(ms_graph), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_graph, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (weights/accumulation); volume storage f32 and bf16",
-        "data": "synthetic (16 seeded problems: Shepp-Logan-shaped phantoms and uniform random fields)",
-        "config": {"workload": "batching form: 16 problems, 96^3..768^3 and 512x512x128, 90..720 views, "
-                               "128^2..768^2 detectors, 5..15 deg half-angles (synth.c5_manifest)",
-                   "samples": samples, "problems": len(items)},
-        "ms": {"separate_launches": round(ms_sep, 3), "batched": round(ms_batch, 3),
-               "batched_autotuned": round(ms_tuned, 3), "batched_autotuned_graph": round(ms_graph, 3)},
-        "gsamples_s": {"separate_launches": gsps(ms_sep), "batched": gsps(ms_batch),
-                       "batched_autotuned": gsps(ms_tuned), "batched_autotuned_graph": gsps(ms_graph)},
-        "speedup_vs_separate": round(ms_sep / ms_graph, 3),
-        "tuning": [{"tile_u": t, "view_group": v} for t, v in tunings],
+        "metric": METRIC + " (batching form)", "value": out["gsamples_s"]["batched_autotuned_graph"], "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["batched_autotuned_graph"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (weights/accumulation); volume storage f32 and bf16",
+        "data": "synthetic (seeded problems: Shepp-Logan-shaped phantoms and uniform random fields)",
+        "config": {"workload": name, "samples": samples, "problems": len(specs)},
+        **out, "tuning": [{"tile_u": t, "view_group": v} for t, v in tunings],
         "clocks": clocks, "gpu_launches": args.steps,
     }), flush=True)
 
 
 def main(argv=None):
     args = parse_args(argv)
-    if args.impl == "reference":
+    if args.ncu_summary:
+        rec = ncu_summary(args.ncu_summary, args.ncu_views, args.ncu_command, args.n, args.views)
+        with open(os.path.join(ROOT, COUNTERS), "w") as f:
+            json.dump(rec, f, indent=1)
+            f.write("\n")
+        print(json.dumps({k: sorted(v) for k, v in rec["kernels"].items()}))
+    elif args.oracle_leg:
+        run_oracle_leg(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
