@@ -378,9 +378,11 @@ gjp_status gjp_batch_forward(const gjp_batch *b, void *stream);
  * problem alone on its first 24 views for each tile shape (tile_u = 1, 2 or
  * 4 detector columns x 128/tile_u rows) and view interleaving (1, 4, 8, 16
  * views), `reps` timed runs after one warm-up each, and keeps the fastest.
- * Writes those views' projections (valid results) and synchronises
- * `stream`; not for use during stream capture.  The choice changes speed
- * only, never a result.
+ * Shapes that are fastest alone need not be fastest in the shared queue:
+ * the whole batch is timed before and after, and the previous shapes are
+ * restored if the tuned ones are slower.  Writes valid projections and
+ * synchronises `stream`; not for use during stream capture.  The choice
+ * changes speed only, never a result.
  */
 gjp_status gjp_batch_autotune(gjp_batch *b, void *stream, int reps);
 

@@ -28,10 +28,6 @@ namespace {
 constexpr int kBatchWarps = 4;                       // one block: 4 warps, 128 rays
 constexpr int kBatchThreads = kBatchWarps * 32;
 constexpr size_t kBatchRowBytes = kBatchWarps * 32 * sizeof(uint2);   // dynamic shared: row tables
-#ifndef GJP_BATCH_CHUNK
-#define GJP_BATCH_CHUNK 1
-#endif
-constexpr int kBatchChunk = GJP_BATCH_CHUNK;         // items taken per queue fetch
 constexpr int kBatchMaxProblems = 256;
 constexpr int kTuneViews = 24;                       // views timed per autotuner candidate
 
@@ -81,43 +77,54 @@ __device__ __forceinline__ void batch_item_i(const BatchProblem &P, int tile, in
 }
 
 // begins[p] = first queue index of problem p, begins[n_probs] = total.
+// Each block takes one item at a time from the queue.
 template <bool ANY_I64, bool ANY_SPL>
 __global__ void __launch_bounds__(kBatchThreads, 8) gjp_batch_forward_kernel(
     const BatchProblem *__restrict__ probs, const long long *__restrict__ begins, int n_probs,
-    unsigned long long *__restrict__ counter, int chunk)
+    unsigned long long *__restrict__ counter)
 {
     // Everything the loop needs across an item lives in shared memory or
     // kernel parameters, so the march keeps the whole register budget (as
     // in the one-problem kernel) and the item's loads stay in flight.
     __shared__ long long s_begin[kBatchMaxProblems + 1];
-    __shared__ long long s_it, s_end;                  // the block's item and the end of its fetched range
+    __shared__ long long s_it;                         // the block's item
     __shared__ BatchProblem s_prob;                    // the item's problem
+    __shared__ int s_lo, s_new;                        // its index; whether the item starts another problem
     for (int k = threadIdx.x; k <= n_probs; k += blockDim.x) s_begin[k] = begins[k];
-    if (threadIdx.x == 0) s_it = s_end = 0;
+    if (threadIdx.x == 0) s_lo = -1;
     for (;;) {
         __syncthreads();                               // the last item's rays are done
         if (threadIdx.x == 0) {
-            long long it = s_it + 1;
-            if (it >= s_end) {                         // range used up (or none yet): fetch
-                it = (long long)atomicAdd(counter, (unsigned long long)chunk);
-                s_end = it + chunk;
-            }
+            const long long it = (long long)atomicAdd(counter, 1ull);
             s_it = it;
+            // the item's problem: found only when it differs from the last
+            // item's (queue positions ascend, so a block's items mostly
+            // stay in one problem)
+            int lo = s_lo;
+            const bool fresh = it < s_begin[n_probs] && (lo < 0 || it >= s_begin[lo + 1]);
+            if (fresh) {
+                int a = 0, b = n_probs - 1;            // last problem with begin <= it
+                while (a < b) {
+                    const int mid = (a + b + 1) >> 1;
+                    if (s_begin[mid] <= it) a = mid;
+                    else b = mid - 1;
+                }
+                lo = a;
+            }
+            s_lo = lo;
+            s_new = fresh ? 1 : 0;
         }
         __syncthreads();
         const long long it = s_it;
         if (it >= s_begin[n_probs]) break;             // queue exhausted (block-uniform)
-        int lo = 0, hi = n_probs - 1;                  // last problem with begin <= it
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_begin[mid] <= it) lo = mid;
-            else hi = mid - 1;
+        const int lo = s_lo;
+        if (s_new) {                                   // block-uniform: copy the new problem's record
+            constexpr int kWords = (int)(sizeof(BatchProblem) / sizeof(long long));
+            if (threadIdx.x < kWords)
+                reinterpret_cast<long long *>(&s_prob)[threadIdx.x] =
+                    reinterpret_cast<const long long *>(probs + lo)[threadIdx.x];
+            __syncthreads();
         }
-        constexpr int kWords = (int)(sizeof(BatchProblem) / sizeof(long long));
-        if (threadIdx.x < kWords)
-            reinterpret_cast<long long *>(&s_prob)[threadIdx.x] =
-                reinterpret_cast<const long long *>(probs + lo)[threadIdx.x];
-        __syncthreads();
         const BatchProblem &P = s_prob;
         // item -> (tile, view): block_tile_view's numbering for one problem
         const long long local = it - s_begin[lo];
@@ -148,7 +155,7 @@ void shape_problem(BatchProblem &P, int tile_u, int view_group, int n_views)
     P.items = (long long)n_views * P.n_tu * P.n_tr;
 }
 
-using BatchKernel = void (*)(const BatchProblem *, const long long *, int, unsigned long long *, int);
+using BatchKernel = void (*)(const BatchProblem *, const long long *, int, unsigned long long *);
 
 BatchKernel batch_kernel(bool any_i64, bool any_spl)
 {
@@ -193,7 +200,7 @@ gjp_status launch(const gjp_batch *b, const BatchProblem *d_probs, const long lo
                   cudaStream_t s)
 {
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return GJP_ERR_CUDA;
-    b->kernel<<<b->grid, kBatchThreads, kBatchRowBytes, s>>>(d_probs, d_begins, n, b->d_counter, kBatchChunk);
+    b->kernel<<<b->grid, kBatchThreads, kBatchRowBytes, s>>>(d_probs, d_begins, n, b->d_counter);
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
@@ -365,6 +372,27 @@ gjp_status gjp_batch_autotune(gjp_batch *b, void *stream, int reps)
     static const int tiles[] = {1, 2, 4};
     static const int groups[] = {1, 4, 8, 16};
     gjp_status st = GJP_OK;
+    // the whole batch, timed as it is now: per-problem shapes that are
+    // fastest alone need not be fastest in the shared queue, so the tuned
+    // shapes are kept only if the whole batch gets faster
+    const int n = (int)b->probs.size();
+    auto batch_ms = [&](float &out) {
+        float ms_min = 3.0e38f;
+        for (int r = 0; r <= reps && st == GJP_OK; ++r) {           // r = 0 warms up
+            if (cudaEventRecord(e0, s) != cudaSuccess) st = GJP_ERR_CUDA;
+            if (st == GJP_OK) st = launch(b, b->d_probs, b->d_begins, n, s);
+            if (st == GJP_OK && cudaEventRecord(e1, s) != cudaSuccess) st = GJP_ERR_CUDA;
+            float ms = 0.0f;
+            if (st == GJP_OK &&
+                (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = GJP_ERR_CUDA;
+            if (r > 0) ms_min = std::min(ms_min, ms);
+        }
+        out = ms_min;
+    };
+    const std::vector<BatchProblem> before = b->probs;
+    float ms_before = 0.0f;
+    batch_ms(ms_before);
     for (size_t q = 0; q < b->probs.size() && st == GJP_OK; ++q) {
         float best = 3.0e38f;
         int best_t = b->probs[q].tile_u, best_g = b->probs[q].view_group;
@@ -394,10 +422,16 @@ gjp_status gjp_batch_autotune(gjp_batch *b, void *stream, int reps)
             }
         shape_problem(b->probs[q], best_t, best_g, b->full_views[q]);
     }
+    if (st == GJP_OK) st = upload(b->probs.data(), n, b->d_probs, b->d_begins);
+    float ms_after = 0.0f;
+    if (st == GJP_OK) batch_ms(ms_after);
+    if (st == GJP_OK && ms_after > ms_before) {                 // keep the shapes it had
+        b->probs = before;
+        st = upload(b->probs.data(), n, b->d_probs, b->d_begins);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st != GJP_OK) return st;
-    return upload(b->probs.data(), (int)b->probs.size(), b->d_probs, b->d_begins);
+    return st;
 }
 
 }  // extern "C"

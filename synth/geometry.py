@@ -249,15 +249,16 @@ def c5_manifest(seed: int = 5, count: int = 16):
 
 
 def small_batch_manifest(seed: int = 6, count: int = 64):
-    """Batching form, many small problems: ``count`` problems from
-    ``numpy.random.default_rng(seed)`` with cubic volumes of 64 .. 192
-    voxels, 16 .. 96 views and square detectors of 64 .. 224 pixels, so
-    that a single problem's launch covers a few waves of the GPU's resident
-    blocks at most and its last wave runs part-empty; float32 or bfloat16
+    """Batching form, many small problems: ``count`` few-view problems from
+    ``numpy.random.default_rng(seed)`` (tomosynthesis-like: 2 .. 16 views)
+    with cubic volumes of 96 .. 192 voxels and square detectors of 96 .. 192
+    pixels.  One problem's launch has 144 .. 4608 blocks of 128 rays, up to
+    about four waves of a GB300's resident blocks and mostly less than one,
+    so separate launches leave the GPU partly idle; float32 or bfloat16
     storage, cone half-angle in [5, 15] degrees, phantom or random-field
     contents."""
     rng = np.random.default_rng(seed)
-    edges = [64, 96, 128, 160, 192]
+    edges = [96, 128, 160, 192]
     out = []
     for k in range(count):
         e = int(rng.choice(edges))
@@ -265,8 +266,8 @@ def small_batch_manifest(seed: int = 6, count: int = 64):
             n=(e, e, e),
             dtype=str(rng.choice(["float32", "bfloat16"])),
             half_angle=float(rng.uniform(5.0, 15.0)),
-            views=int(rng.integers(16, 97)),
-            det=int(rng.integers(64, 225)),
+            views=int(rng.integers(2, 17)),
+            det=int(rng.integers(96, 193)),
             content=str(rng.choice(["phantom", "random"])),
             seed=2000 + k))
     return out

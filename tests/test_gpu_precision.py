@@ -3,10 +3,14 @@ bfloat16 and float16 (float32 weights and accumulation), projected on the
 1024^3 / 1024^2 / 720-view and 2048^3 / 2048^2 / 64-view workloads.
 
 Errors are measured against the FP64 oracle evaluated on the unquantised
-float32 volume, on sampled rays of an evenly spaced subset of (at most) 128
-views: max error relative to the largest reference value (bound 1e-5 for
-float32 storage, 5e-3 for 16-bit storage) and RMS error.  With
-GJP_REPORT_DIR set, the error table is written there as JSON.
+float32 volume, on every view of an evenly spaced subset of (at most) 128
+views, each on a strided 64 x 64 grid of its detector pixels (shifted from
+view to view so that the views together take every residue of the
+stride in u and in v): max error relative to the largest reference value (bound 1e-5 for
+float32 storage, 5e-3 for 16-bit storage) and RMS error.  Rays whose two
+largest direction components are within 1e-5 may take either driving axis
+(reading C2).  The 2048^3 phantom is voxelised without supersampling (host
+time).  With GJP_REPORT_DIR set, the error table is written there as JSON.
 """
 import json
 import os
@@ -39,6 +43,20 @@ def _host_gb():
         return 0.0
 
 
+def strided_rays(cg, m):
+    """(views, ius, ivs) of an m x m grid of pixels on every view, the grid
+    shifted by a view-dependent offset within the stride."""
+    su, sv = max(1, cg.nu // m), max(1, cg.nv // m)
+    vs, us, ws = [], [], []
+    for k in range(cg.n_views):
+        ou, ov = (7 * k) % su, (3 * k) % sv
+        iv, iu = np.meshgrid(np.arange(ov, cg.nv, sv)[:m], np.arange(ou, cg.nu, su)[:m], indexing="ij")
+        vs.append(np.full(iu.size, k))
+        us.append(iu.ravel())
+        ws.append(iv.ravel())
+    return np.concatenate(vs), np.concatenate(us), np.concatenate(ws)
+
+
 @pytest.mark.parametrize("n", [1024, 2048])
 def test_precision_form(gjp, n):
     vol_gb = n ** 3 * 4 / 2 ** 30
@@ -50,7 +68,7 @@ def test_precision_form(gjp, n):
     cg = cg_all.subset(views)
     vol = synth.voxelize(vg, supersample=2 if n <= 1024 else 1)
     g = gjp.Geometry.from_cone(cg)
-    rays = parity.sampled_rays(cg, 1500, seed=n)
+    rays = strided_rays(cg, 64)
     ref = oracle.rays(vol, vg, cg, *rays)
     scale = np.abs(ref).max()
     table = {}
@@ -64,13 +82,12 @@ def test_precision_form(gjp, n):
         del out
         if name != "float32":
             del dv
-        err = np.abs(got - ref)
-        table[name] = {"max_rel": float(err.max() / scale), "rms_rel": float(np.sqrt(np.mean(err ** 2)) / scale)}
-        assert table[name]["max_rel"] <= BOUND[name], (name, table[name])
+        res = parity.check_rays(got, vol, vg, cg, *rays, scale, BOUND[name], ref=ref)
+        table[name] = {"max_rel": res["max_rel"], "rms_rel": res["rms_rel"], "ties": res["ties"]}
     # 16-bit storage keeps most of the float32 accuracy budget: bf16 rounds
     # to 8 significant bits, fp16 to 11
     assert table["float16"]["max_rel"] < table["bfloat16"]["max_rel"]
     out_dir = os.environ.get("GJP_REPORT_DIR")
     if out_dir:
         with open(os.path.join(out_dir, f"precision_{n}.json"), "w") as f:
-            json.dump({"n": n, "views": int(len(views)), "rays": 1500, "errors": table}, f, indent=1)
+            json.dump({"n": n, "views": int(len(views)), "rays": int(rays[0].size), "errors": table}, f, indent=1)
