@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import _capi
+from . import _capi, tuning_cache
 from ._capi import GjpError
 
 __all__ = ["Geometry", "Batch", "forward", "adjoint", "footprint_voxels", "stream_status", "GjpError",
@@ -36,7 +36,9 @@ class Geometry:
         if st != _capi.GJP_OK:
             raise GjpError(st, "gjp_geometry_create")
         self.handle = h
+        self.digest = tuning_cache.geometry_digest(src, det_origin, det_u, det_v, self.nu, self.nv)
         self.weight = "lin"
+        self.fov = 0.0
         if weight != "lin":
             self.set_weight(weight)
 
@@ -214,6 +216,7 @@ class Batch:
     def __init__(self, problems):
         torch = _torch()
         self._keep = []
+        self._sigs = []
         recs = []
         self.device = None
         for vol, geom, h, origin, out in problems:
@@ -239,6 +242,9 @@ class Batch:
             r.d_proj = out.data_ptr()
             recs.append(r)
             self._keep.append((vol, geom, out))
+            self._sigs.append(tuning_cache.problem_signature(str(vol.dtype).replace("torch.", ""), vol.shape, h,
+                                                             origin, geom.digest, geom.weight,
+                                                             getattr(geom, "fov", 0.0)))
         self.handle = None
         with torch.cuda.device(self.device):
             st, h = _capi.gjp_batch_create(recs)
@@ -256,14 +262,29 @@ class Batch:
             raise GjpError(st, "gjp_batch_forward")
         return self.outputs
 
-    def autotune(self, reps: int = 2, stream=None):
+    def autotune(self, reps: int = 2, stream=None, cache: str | None = None):
+        """Launch-shape search (``gjp_batch_autotune``).  With ``cache`` (a
+        JSON file path), shapes found before for the same GPU model and the
+        same problems are read from it instead of timed again, and new ones
+        are added to it.  Returns the ``(tile_u, view_group)`` per problem."""
         torch = _torch()
+        gpu = torch.cuda.get_device_name(self.device)
+        key = tuning_cache.batch_key(gpu, self._sigs) if cache else None
+        if cache:
+            hit = tuning_cache.lookup(cache, key, len(self._keep))
+            if hit is not None:
+                for i, (t, v) in enumerate(hit):
+                    self.set_tuning(i, t, v)
+                return hit
         with torch.cuda.device(self.device):
             s = torch.cuda.current_stream(self.device) if stream is None else stream
             st = _capi.gjp_batch_autotune(self.handle, int(s.cuda_stream), reps)
         if st != _capi.GJP_OK:
             raise GjpError(st, "gjp_batch_autotune")
-        return [self.tuning(i) for i in range(len(self._keep))]
+        tunings = [self.tuning(i) for i in range(len(self._keep))]
+        if cache:
+            tuning_cache.store(cache, key, gpu, tunings)
+        return tunings
 
     def tuning(self, i: int):
         st, tu, vg = _capi.gjp_batch_get_tuning(self.handle, i)

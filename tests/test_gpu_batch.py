@@ -126,6 +126,29 @@ def test_batch_autotune_changes_no_result(gjp):
         batch.tuning(len(items))
 
 
+def test_batch_autotune_cache(gjp, tmp_path, monkeypatch):
+    """Shapes found once are read back from the cache file for the same GPU
+    and problems, without timing; another batch is a miss."""
+    from paper_1609_00958_gb300 import _capi
+    probs = _small_problems(gjp)[:3]
+    items = _batch_inputs(gjp, probs)
+    cache = str(tmp_path / "tunings.json")
+    first = gjp.Batch(items).autotune(reps=1, cache=cache)
+
+    def no_timing(*args, **kwargs):
+        raise AssertionError("the search ran although the cache holds this batch")
+
+    monkeypatch.setattr(_capi, "gjp_batch_autotune", no_timing)
+    again = gjp.Batch(items)
+    assert again.autotune(reps=1, cache=cache) == first
+    assert [again.tuning(i) for i in range(len(items))] == first
+    ref = [gjp.forward(vol, g, h, origin) for vol, g, h, origin, _ in items]
+    for r, o in zip(ref, again.forward()):
+        assert torch.equal(r, o)
+    with pytest.raises(AssertionError):                 # two of the three problems: not cached
+        gjp.Batch(items[:2]).autotune(reps=1, cache=cache)
+
+
 def test_batch_rejects_invalid_problems(gjp):
     vg = VolumeGeometry.centred((16, 16, 16))
     vol = torch.zeros(vg.n, device="cuda")
