@@ -237,6 +237,17 @@ gjp_status gjp_selftest_wait_timeout(void *stream);
 gjp_status gjp_selftest_tap_check(void *stream);
 
 /*
+ * gjp_debug_fail_allocations -- failure-injection hook for tests (the paper
+ * has no counterpart): the next `n` device allocations that the library
+ * attempts (per-view tables, batch queues, texture arrays) fail as if the
+ * device were out of memory, so the calls that need them return
+ * GJP_ERR_OOM and leave their outputs untouched; later allocations proceed.
+ * n = 0 clears it.  Host-only, thread-safe; no GPU fault is involved.
+ * Returns GJP_ERR_INVALID_ARG for n < 0.
+ */
+gjp_status gjp_debug_fail_allocations(int n);
+
+/*
  * gjp_adjoint -- matched transpose of gjp_forward (float32 volume):
  * d_volume (+)= A^T d_proj, where A is the system matrix of gjp_forward
  * (the g = A f view of the reconstruction section).  Every (ray, plane,

@@ -33,9 +33,21 @@
 //    that accompanies Algorithm 1).
 #include "gjp_common.cuh"
 
+#include <atomic>
+
 namespace gjp_detail {
 
 bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+std::atomic<int> g_fail_allocations{0};
+
+bool alloc_gate()
+{
+    int n = g_fail_allocations.load();
+    while (n > 0)
+        if (g_fail_allocations.compare_exchange_weak(n, n - 1)) return false;
+    return true;
+}
 
 void split(double x, float &hi, float &lo)
 {
@@ -103,7 +115,7 @@ gjp_status get_table(const gjp_geometry *gc, const int64_t n[3], const double h[
     }
     ViewParams *d = nullptr;
     const size_t bytes = sizeof(ViewParams) * host.size();
-    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    if (!alloc_gate() || cudaMalloc(&d, bytes) != cudaSuccess) {
         cudaGetLastError();
         return GJP_ERR_OOM;
     }
@@ -1729,6 +1741,7 @@ gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int
                           const double voxel_size[3], const double volume_origin[3], const gjp_geometry *g,
                           float *d_proj, gjp_path path, void *stream)
 {
+    NvtxRange nvtx_range("gjp_forward");
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
     if (dtype != GJP_F32 && dtype != GJP_BF16 && dtype != GJP_F16) return GJP_ERR_INVALID_ARG;
     if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_PREFETCH &&
@@ -1763,6 +1776,7 @@ gjp_status gjp_forward_noalloc(const void *d_volume, gjp_dtype dtype, int64_t nx
                                const double voxel_size[3], const double volume_origin[3], const gjp_geometry *g,
                                float *d_proj, void *stream)
 {
+    NvtxRange nvtx_range("gjp_forward_noalloc");
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
     if (dtype != GJP_F32 && dtype != GJP_BF16 && dtype != GJP_F16) return GJP_ERR_INVALID_ARG;
     int64_t n[3];
@@ -1806,6 +1820,13 @@ gjp_status gjp_selftest_wait_timeout(void *stream)
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
 
+gjp_status gjp_debug_fail_allocations(int n)
+{
+    if (n < 0) return GJP_ERR_INVALID_ARG;
+    g_fail_allocations.store(n);
+    return GJP_OK;
+}
+
 gjp_status gjp_selftest_tap_check(void *stream)
 {
     if (!GJP_CHECK_TAPS) return GJP_ERR_UNSUPPORTED;
@@ -1834,6 +1855,7 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
                           const double voxel_size[3], const double volume_origin[3], float *d_volume,
                           int accumulate, gjp_path path, void *stream)
 {
+    NvtxRange nvtx_range("gjp_adjoint");
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
     if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_COMBINE)
         return GJP_ERR_INVALID_ARG;
@@ -1918,6 +1940,7 @@ gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny
                          const double voxel_size[3], const double volume_origin[3],
                          unsigned char *d_marks, void *stream)
 {
+    NvtxRange nvtx_range("gjp_footprint");
     if (!g || !d_marks || view < 0 || view >= g->n_views) return GJP_ERR_INVALID_ARG;
     int64_t n[3];
     double h[3], o[3];

@@ -229,6 +229,7 @@ extern "C" {
 
 gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **out)
 {
+    NvtxRange nvtx_range("gjp_batch_create");
     if (!out) return GJP_ERR_INVALID_ARG;
     *out = nullptr;
     if (!problems || count < 1 || count > kBatchMaxProblems) return GJP_ERR_INVALID_ARG;
@@ -289,7 +290,7 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
         b->full_views.push_back(host[p].n_views);
     }
     const size_t pb = sizeof(BatchProblem) * count, bb = sizeof(long long) * (count + 1);
-    if (cudaMalloc(&b->d_probs, pb) != cudaSuccess || cudaMalloc(&b->d_begins, bb) != cudaSuccess ||
+    if (!alloc_gate() || cudaMalloc(&b->d_probs, pb) != cudaSuccess || cudaMalloc(&b->d_begins, bb) != cudaSuccess ||
         cudaMalloc(&b->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&b->d_tune, sizeof(BatchProblem)) != cudaSuccess ||
         cudaMalloc(&b->d_tune_begins, 2 * sizeof(long long)) != cudaSuccess) {
@@ -325,6 +326,7 @@ void gjp_batch_destroy(gjp_batch *b) { free_batch(b); }
 
 gjp_status gjp_batch_forward(const gjp_batch *b, void *stream)
 {
+    NvtxRange nvtx_range("gjp_batch_forward");
     if (!b) return GJP_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GJP_ERR_CUDA;
@@ -359,6 +361,7 @@ gjp_status gjp_batch_set_tuning(gjp_batch *b, int problem, int tile_u, int view_
 
 gjp_status gjp_batch_autotune(gjp_batch *b, void *stream, int reps)
 {
+    NvtxRange nvtx_range("gjp_batch_autotune");
     if (!b || reps < 1) return GJP_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GJP_ERR_CUDA;

@@ -8,6 +8,7 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -143,6 +144,18 @@ size_t elem_size(gjp_dtype t);
 gjp_status forward_texture(const void *d_volume, gjp_dtype dt, const int64_t n[3], const VolParams &V,
                            const gjp_geometry &g, gjp_cache_entry &entry, float *proj, int path, cudaStream_t s);
 void free_texture_cache(gjp_cache_entry &e);
+// Every device allocation of the library asks alloc_gate() first: false
+// makes it fail as if the device were out of memory.  That happens only for
+// the next n allocations after gjp_debug_fail_allocations(n), a test hook
+// for the out-of-memory paths.
+bool alloc_gate();
+// An NVTX range around an entry point (no cost without a profiler attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 // Tap-check faults recorded by the kernels of the other translation units
 // (debug build; 0 otherwise), read and cleared.
 unsigned batch_tap_faults();

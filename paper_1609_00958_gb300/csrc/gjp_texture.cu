@@ -126,8 +126,9 @@ gjp_status ensure_arrays(gjp_cache_entry &e, gjp_dtype dt, const int64_t n[3], b
     }
     const cudaChannelFormatDesc ch = channel(dt);
     if (hw && !c->vol3d) {
-        if (cudaMalloc3DArray(&c->vol3d, &ch, make_cudaExtent((size_t)n[2], (size_t)n[1], (size_t)n[0]), 0) !=
-            cudaSuccess) {
+        if (!alloc_gate() ||
+            cudaMalloc3DArray(&c->vol3d, &ch, make_cudaExtent((size_t)n[2], (size_t)n[1], (size_t)n[0]), 0) !=
+                cudaSuccess) {
             cudaGetLastError();
             c->vol3d = nullptr;
             return GJP_ERR_OOM;
@@ -136,7 +137,8 @@ gjp_status ensure_arrays(gjp_cache_entry &e, gjp_dtype dt, const int64_t n[3], b
     }
     if (!hw && !c->layered_x) {
         // planes x = i: (columns z, rows y, layers x); planes y = j: (columns z, rows x, layers y)
-        if (cudaMalloc3DArray(&c->layered_x, &ch, make_cudaExtent((size_t)n[2], (size_t)n[1], (size_t)n[0]),
+        if (!alloc_gate() ||
+            cudaMalloc3DArray(&c->layered_x, &ch, make_cudaExtent((size_t)n[2], (size_t)n[1], (size_t)n[0]),
                               cudaArrayLayered) != cudaSuccess ||
             cudaMalloc3DArray(&c->layered_y, &ch, make_cudaExtent((size_t)n[2], (size_t)n[0], (size_t)n[1]),
                               cudaArrayLayered | cudaArraySurfaceLoadStore) != cudaSuccess) {

@@ -139,3 +139,11 @@ def test_batch_create_rejects_bad_arguments_without_a_gpu(lib):
     assert _capi.gjp_batch_autotune(None, 0, 1) == _capi.GJP_ERR_INVALID_ARG
     assert _capi.gjp_batch_get_tuning(None, 0)[0] == _capi.GJP_ERR_INVALID_ARG
     _capi.gjp_batch_destroy(None)
+
+
+def test_debug_fail_allocations_arguments(lib):
+    """The out-of-memory injection hook is host-only: it takes a count and
+    rejects a negative one (its effect is tested on the GPU)."""
+    assert _capi.gjp_debug_fail_allocations(-1) == _capi.GJP_ERR_INVALID_ARG
+    assert _capi.gjp_debug_fail_allocations(3) == _capi.GJP_OK
+    assert _capi.gjp_debug_fail_allocations(0) == _capi.GJP_OK
