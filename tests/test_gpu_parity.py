@@ -393,6 +393,25 @@ def test_c2_full_size_sampled(gjp, content, path):
     parity.check_rays(gpu[views, ivs, ius], vol, vg, cg, views, ius, ivs, np.abs(ref).max(), TOL32, ref=ref)
 
 
+def test_adjoint_full_size_against_oracle(gjp):
+    """The 512^3 / 512^2 adjoint (combined family: row table, run form) of
+    two whole views against the oracle's transpose of the same projections.
+    Views 10 and 100 hold no driving-axis ties (their rays run within 20
+    degrees of an axis), so every ray's taps are the oracle's."""
+    vg, cg = synth.c2_geometry()
+    sub = cg.subset([10, 100])
+    g = gjp.Geometry.from_cone(sub)
+    vol = synth.random_field(vg.n, seed=0)
+    y = gjp.forward(torch.from_numpy(vol).cuda(), g, vg.h)
+    back = gjp.adjoint(y, g, vg.n, vg.h).cpu().numpy()
+    gjp.stream_status()
+    ref = oracle.adjoint(y.cpu().numpy().astype(np.float64), vg, sub, max_bytes=16e9)
+    err = np.abs(back - ref)
+    scale = np.abs(ref).max()
+    assert scale > 0
+    assert err.max() <= TOL32 * scale, err.max() / scale
+
+
 def test_exact_driving_axis_ties(gjp):
     """Rays with |r_x| == |r_y| exactly (reading C2: ties go to the lowest
     axis; either axis is accepted where float32 could see a near-tie)."""
