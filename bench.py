@@ -568,10 +568,10 @@ def run_gjp(args):
         result["kernels_phantom"] = phantom_kernels(args, gjp, geom, vg, cg, dev, stream, hbm, peak_kind, k16)
     if world == 1 and not args.no_batch and not args.first_views:
         name, make = BATCH_MIXES["small"]
-        ms, samples, tunings, _ = batch_measure(make(), args.warmup, max(1, min(args.steps, 10)), dev)
+        ms, samples, _, _ = batch_measure(make(), args.warmup, max(1, min(args.steps, 10)), dev)
         result["batching_small"] = {"workload": name, "samples": samples, **batch_summary(ms, samples)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(args, gjp, geom, vg, cg, vol_np, counts, proj32, proj16, dev)
+        result["cpu_baseline"] = cpu_baseline(args, gjp, vg, cg, proj32, proj16)
         if "error_vs_oracle" in result["cpu_baseline"]:
             result["error_vs_oracle"] = result["cpu_baseline"].pop("error_vs_oracle")
     if rank == 0:
@@ -783,7 +783,7 @@ def _worst(es):
             "rms_rel": float(f"{np.sqrt(np.mean([e['rms_rel'] ** 2 for e in es])):.3e}")}
 
 
-def oracle_leg(args, vg, cg, vol_np, counts, blocks, warm_blocks, gpu=None):
+def oracle_leg(vg, cg, vol_np, counts, blocks, warm_blocks, gpu=None):
     """The oracle timed on the host cores: ``warm_blocks`` untimed blocks,
     then ``blocks`` timed, each block of views in three oracle calls.  With
     ``gpu`` (per block: GPU float32 and bfloat16 projections of the block's
@@ -830,7 +830,7 @@ def baseline_blocks(n_views, n_blocks):
     return blocks[1:], blocks[:1]
 
 
-def cpu_baseline(args, gjp, geom, vg, cg, vol_np, counts, proj32, proj16, dev):
+def cpu_baseline(args, gjp, vg, cg, proj32, proj16):
     """The oracle on the host cores over ``--oracle-blocks`` blocks of
     ORACLE_BLOCK views, after one warm-up block: the reference arm's
     procedure, run in a fresh child process (no CUDA) so that both legs time
@@ -884,7 +884,7 @@ def run_oracle_leg(args):
     gpu = [(np.load(os.path.join(args.oracle_leg, f"p32_{bi}.npy")),
             np.load(os.path.join(args.oracle_leg, f"p16_{bi}.npy")),
             np.load(os.path.join(args.oracle_leg, f"back_{bi}.npy"))) for bi in range(len(spec["blocks"]))]
-    out = oracle_leg(args, vg, cg, vol_np, counts, spec["blocks"], spec["warm"], gpu=gpu)
+    out = oracle_leg(vg, cg, vol_np, counts, spec["blocks"], spec["warm"], gpu=gpu)
     print(json.dumps(out), flush=True)
 
 
@@ -904,7 +904,7 @@ def run_reference(args):
     views = oracle_views(cg.n_views, ORACLE_BLOCK * n_steps)
     blocks = [views[i::n_steps][:ORACLE_BLOCK] for i in range(n_steps)]   # each block spans the scan
     warm = blocks[:n_steps - args.steps]
-    leg = oracle_leg(args, vg, cg, vol_np, counts, blocks[len(warm):], warm)
+    leg = oracle_leg(vg, cg, vol_np, counts, blocks[len(warm):], warm)
     value, total_t, threads = leg["value"], leg["seconds"], leg["threads"]
     sample = (f"one block of {ORACLE_BLOCK} views per step (forward f32 + forward bf16-stored + adjoint, "
               f"one oracle call each), {args.steps} blocks spread over the scan after {len(warm)} warm-up "
