@@ -59,8 +59,9 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gjp", "reference"], default="gjp")
-    p.add_argument("--workload", choices=["step", "batch"], default="step",
-                   help="step: the 512^3 hot-path step (default); batch: the 16-problem batching workload")
+    p.add_argument("--workload", choices=["step", "batch", "cgls"], default="step",
+                   help="step: the 512^3 hot-path step (default); batch: the batching workload; "
+                        "cgls: the 256^3 differentiation form (CGLS and an autograd step)")
     p.add_argument("--batch-mix", choices=["c5", "small"], default="c5",
                    help="problems of --workload batch: the 16-problem c5 mix or 64 small problems")
     p.add_argument("--no-batch", action="store_true", help="skip the small-problem batching figures of the step")
@@ -1037,6 +1038,75 @@ def run_batch(args):
     }), flush=True)
 
 
+def run_cgls(args):
+    """The differentiation form: 256^3 Shepp-Logan-shaped phantom, 256^2
+    detector, 180 views (10 degree half-angle).  Times (a) 30 CGLS
+    iterations (one forward and one adjoint each, plus the solver's dot
+    products and updates) and (b) a gradient step through the autograd
+    function (forward, squared-error loss, backward = adjoint).  The data
+    are the GPU projections of the phantom itself: this times the solver;
+    reconstruction quality from closed-form analytic projections is the
+    tests' job.  One JSON line; ``value`` is (a) in Gsamples/s."""
+    import torch
+    from paper_1609_00958_gb300 import build as libbuild
+    libbuild.build()
+    import paper_1609_00958_gb300 as gjp
+    from paper_1609_00958_gb300.autograd import project
+    from paper_1609_00958_gb300.recon import cgls
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    vg, cg = synth.c4_geometry()
+    g = gjp.Geometry.from_cone(cg)
+    x_true = torch.from_numpy(synth.voxelize(vg, supersample=2)).to(dev)
+    b = gjp.forward(x_true, g, vg.h)
+    samples = int(sample_counts(vg, cg).sum())
+    n_iter = 30
+    # warm-up with the same arguments: the first call of each torch kernel of
+    # the solver's bookkeeping can include its JIT compilation (seconds)
+    cgls(b, g, vg.n, 2, vg.h, x_true=x_true)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id_for_smi(0)) as clk:
+        t0 = time.perf_counter()
+        x, hist = cgls(b, g, vg.n, n_iter, vg.h, x_true=x_true)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    ms_iter = 1e3 * wall / n_iter
+    # a training-style step: loss on the projections, gradient into the volume
+    vol = torch.zeros(vg.n, device=dev, requires_grad=True)
+
+    def grad_step():
+        vol.grad = None
+        loss = 0.5 * torch.sum((project(vol, g, vg.h) - b) ** 2)
+        loss.backward()
+        return loss
+
+    for _ in range(max(1, args.warmup)):
+        grad_step()
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        grad_step()
+    e.record()
+    torch.cuda.synchronize()
+    ms_grad = a.elapsed_time(e) / args.steps
+    pick = [0, 10, 20, 30]
+    print(json.dumps({
+        "metric": METRIC + " (differentiation form)", "value": round(2 * samples / (ms_iter * 1e-3) / 1e9, 2),
+        "unit": UNIT, "n_gpus": 1, "steps": n_iter, "warmup": 2, "ms_per_step": round(ms_iter, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (Shepp-Logan-shaped phantom, its own GPU projections)",
+        "config": {"workload": "differentiation form: 256^3 phantom, 256^2 detector, 180 views, 10 deg half-angle, "
+                               "30 CGLS iterations", "samples_per_projection": samples},
+        "cgls": {"ms_per_iteration": round(ms_iter, 3), "iterations": n_iter,
+                 "residual": {str(k): float(f"{hist.residual[k]:.4e}") for k in pick if k < len(hist.residual)},
+                 "rmse": {str(k): float(f"{hist.rmse[k]:.4e}") for k in pick if k < len(hist.rmse)}},
+        "autograd_step_ms": round(ms_grad, 3),
+        "clocks": clocks, "gpu_launches": 2 * n_iter,
+    }), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.ncu_summary:
@@ -1051,6 +1121,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "cgls":
+        run_cgls(args)
     else:
         run_gjp(args)
 
