@@ -104,11 +104,17 @@ gjp_status gjp_geometry_set_weight(gjp_geometry *g, gjp_weight w);
  * is that knob, plus the order in which blocks are issued.
  *   tile_u     : detector columns per block, 1, 2, 4 (default) or 8; a
  *                block is tile_u warps of 32 detector rows.
- *   view_group : 1 .. 64 (default 16).  Blocks are issued so that
- *                view_group consecutive views are processed tile by tile
- *                together (their rays cross nearly the same voxels, which
- *                then come from the L2 cache); 1 issues the views one
- *                after another.
+ *   view_group : 1 .. 64.  Blocks are issued so that view_group
+ *                consecutive views are processed tile by tile together
+ *                (their rays cross nearly the same voxels, which then come
+ *                from the L2 cache); 1 issues the views one after another.
+ *                Until this call is made, each launch picks it from the
+ *                grid and the scan: a group spans 16 degrees of rotation
+ *                at 512 voxels per edge, scaled by (512 / longest edge)^2,
+ *                divided by the median angle between consecutive views'
+ *                central rays and held to 1 .. 16 views (wider groups
+ *                would outgrow the L2); gjp_geometry_get_launch then
+ *                reports 16.
  * Returns GJP_ERR_INVALID_ARG for NULL or a value outside those sets.
  */
 gjp_status gjp_geometry_set_launch(gjp_geometry *g, int tile_u, int view_group);

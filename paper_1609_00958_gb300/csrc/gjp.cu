@@ -83,6 +83,35 @@ void make_view_params(const gjp_geometry &g, int k, const int64_t n[3], const do
     }
 }
 
+// Median angle between the central rays (source to detector centre) of
+// consecutive views: the rotation step of a circular scan (0 for one view).
+double central_ray_step(const gjp_geometry &g)
+{
+    if (g.n_views < 2) return 0.0;
+    std::vector<double> steps;
+    steps.reserve(g.n_views - 1);
+    double prev[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < g.n_views; ++k) {
+        double d[3], nn = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double c = g.org[3 * k + a] + 0.5 * (g.nu - 1) * g.du[3 * k + a] + 0.5 * (g.nv - 1) * g.dv[3 * k + a];
+            d[a] = c - g.src[3 * k + a];
+            nn += d[a] * d[a];
+        }
+        nn = std::sqrt(nn);
+        for (int a = 0; a < 3; ++a) d[a] /= nn;
+        if (k > 0) {
+            const double cx = prev[1] * d[2] - prev[2] * d[1], cy = prev[2] * d[0] - prev[0] * d[2],
+                         cz = prev[0] * d[1] - prev[1] * d[0];
+            const double dot = prev[0] * d[0] + prev[1] * d[1] + prev[2] * d[2];
+            steps.push_back(std::atan2(std::sqrt(cx * cx + cy * cy + cz * cz), dot));
+        }
+        for (int a = 0; a < 3; ++a) prev[a] = d[a];
+    }
+    std::nth_element(steps.begin(), steps.begin() + steps.size() / 2, steps.end());
+    return steps[steps.size() / 2];
+}
+
 // Host FP64 construction of the per-view table for one volume grid.
 void build_table(const gjp_geometry &g, const int64_t n[3], const double h[3], const double o[3],
                  std::vector<ViewParams> &out)
@@ -1390,7 +1419,7 @@ cudaError_t launch_slab(const T *vol, const VolParams &V, const ViewParams *tabl
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, kSlabThreads, smem, s>>>(vol, V, table, g.nu, g.nv, n_tv, g.n_views, g.view_group, mx, my, rows,
+    kern<<<grid, kSlabThreads, smem, s>>>(vol, V, table, g.nu, g.nv, n_tv, g.n_views, launch_view_group(g, V.n), mx, my, rows,
                                           proj);
     return cudaGetLastError();
 }
@@ -1437,11 +1466,11 @@ cudaError_t launch_gather_pf(const T *vol, gjp_dtype dt, const int64_t n[3], con
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
     const dim3 block(kTileV, g.tile_u);
     if (i32)
-        gjp_forward_pf_kernel<T, int><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, g.n_views, g.view_group,
+        gjp_forward_pf_kernel<T, int><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, g.n_views, launch_view_group(g, V.n),
                                                              map, proj);
     else
         gjp_forward_pf_kernel<T, long long><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, g.n_views,
-                                                                   g.view_group, map, proj);
+                                                                   launch_view_group(g, V.n), map, proj);
     launched = true;
     return cudaGetLastError();
 }
@@ -1455,7 +1484,7 @@ cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *ta
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
     const dim3 block(kTileV, g.tile_u);
     const bool spl = g.weight == GJP_WEIGHT_SPL;
-    const int nvw = g.n_views, vgp = g.view_group;
+    const int nvw = g.n_views, vgp = launch_view_group(g, V.n);
     const size_t rows = (size_t)g.tile_u * 32 * sizeof(uint2);   // row tables (32-bit offsets only)
     if (i32) {
         if (spl)
@@ -1531,7 +1560,7 @@ cudaError_t launch_adjoint_slab(const float *proj, const VolParams &V, const Vie
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, kSlabWarps * 32, smem, s>>>(proj, V, table, g.nu, g.nv, n_tv, g.n_views, g.view_group, mx, my,
+    kern<<<grid, kSlabWarps * 32, smem, s>>>(proj, V, table, g.nu, g.nv, n_tv, g.n_views, launch_view_group(g, V.n), mx, my,
                                              rows, vol);
     return cudaGetLastError();
 }
@@ -1673,6 +1702,7 @@ gjp_status gjp_geometry_create(int n_views, int nu, int nv, const double *src, c
         g->org.assign(det_origin, det_origin + 3 * (size_t)n_views);
         g->du.assign(det_u, det_u + 3 * (size_t)n_views);
         g->dv.assign(det_v, det_v + 3 * (size_t)n_views);
+        g->view_step = central_ray_step(*g);
     } catch (const std::bad_alloc &) {
         delete g;
         return GJP_ERR_OOM;
@@ -1710,6 +1740,7 @@ gjp_status gjp_geometry_set_launch(gjp_geometry *g, int tile_u, int view_group)
         return GJP_ERR_INVALID_ARG;
     g->tile_u = tile_u;
     g->view_group = view_group;
+    g->launch_set = true;
     return GJP_OK;
 }
 
@@ -1881,7 +1912,7 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
         const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
         const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
         const dim3 block(kTileV, g->tile_u);
-        const int nvw = g->n_views, vgp = g->view_group;
+        const int nvw = g->n_views, vgp = launch_view_group(*g, n);
         const bool clip = V.fov_r2 > 0.0f;
         const size_t rows = (size_t)g->tile_u * 32 * sizeof(uint2);   // row tables
 #define GJP_COMBINE_LAUNCH(I, S, C)                                                                                \
@@ -1911,7 +1942,7 @@ gjp_status gjp_adjoint_ex(const float *d_proj, const gjp_geometry *g, int64_t nx
     const int n_tu = (g->nu + g->tile_u - 1) / g->tile_u;
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g->n_views);
     const dim3 block(kTileV, g->tile_u);
-    const int nvw = g->n_views, vgp = g->view_group;
+    const int nvw = g->n_views, vgp = launch_view_group(*g, n);
     if (fits_int32(n)) {
         if (spl)
             gjp_adjoint_kernel<int, true><<<grid, block, 0, s>>>(d_proj, V, table, g->nu, g->nv, n_tv, nvw, vgp, d_volume);

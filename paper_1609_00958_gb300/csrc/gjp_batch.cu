@@ -277,7 +277,7 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
         P.nv = q.geometry->nv;
         P.kind = (int)q.dtype | (fits_int32(n) ? 4 : 0) | (q.geometry->weight == GJP_WEIGHT_SPL ? 8 : 0);
         const int tu = valid_tile(q.geometry->tile_u) ? q.geometry->tile_u : 4;
-        shape_problem(P, tu, q.geometry->view_group, q.geometry->n_views);
+        shape_problem(P, tu, launch_view_group(*q.geometry, n), q.geometry->n_views);
         planes[p] = (int)std::max(n[0], std::max(n[1], n[2]));
     }
     // queue order: problems with the longest rays (most planes per item) first

@@ -358,7 +358,7 @@ gjp_status forward_texture(const void *d_volume, gjp_dtype dt, const int64_t n[3
     const int n_tu = (g.nu + g.tile_u - 1) / g.tile_u;
     const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
     const dim3 block(kTileV, g.tile_u);
-    const int nvw = g.n_views, vgp = g.view_group;
+    const int nvw = g.n_views, vgp = launch_view_group(g, V.n);
     if (hw) {
         if (copy_direct(d_volume, es, n, c->vol3d, s) != cudaSuccess) return GJP_ERR_CUDA;
         gjp_forward_hwlin_kernel<<<grid, block, 0, s>>>(c->tex_3d, V, entry.d_table, g.nu, g.nv, n_tv, nvw,
