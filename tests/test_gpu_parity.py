@@ -276,6 +276,32 @@ def test_launch_shape_changes_no_result(gjp):
             g.set_launch(*bad)
 
 
+def test_default_view_group_follows_grid_and_scan(gjp):
+    """Without set_launch, a launch takes its view group from the grid's
+    longest edge and the scan's step between views (16 degrees of rotation
+    at 512 voxels per edge, shrinking like the edge squared).  A long, thin
+    grid (1024 voxels along x) scanned in 0.5 degree steps gets groups of
+    8; that reorders blocks only, so the projections equal those of an
+    explicit launch shape bitwise, and the adjoint agrees to float32
+    rounding."""
+    import math
+    rng = np.random.default_rng(13)
+    vg = VolumeGeometry.centred((1024, 40, 36))
+    angles = [math.radians(0.5 * k) for k in range(20)]
+    cg = synth.circular(20, 48, 40, 2000.0, 4000.0, 1.9, angles=angles)
+    vol = torch.from_numpy(rng.random(vg.n, dtype=np.float32)).cuda()
+    g = gjp.Geometry.from_cone(cg)
+    assert g.launch == (4, 16)                  # the reported setting until set_launch
+    auto = gjp.forward(vol, g, vg.h)
+    back_auto = gjp.adjoint(auto, g, vg.n, vg.h)
+    gjp.stream_status()
+    for launch in ((4, 16), (4, 8), (4, 1)):
+        g.set_launch(*launch)
+        assert torch.equal(gjp.forward(vol, g, vg.h), auto), launch
+        back = gjp.adjoint(auto, g, vg.n, vg.h)
+        assert ((back - back_auto).abs().max() / back_auto.abs().max()).item() < 1e-6, launch
+
+
 def test_adjoint_accumulate(gjp):
     rng = np.random.default_rng(5)
     vg = VolumeGeometry.centred((20, 18, 16))
