@@ -569,8 +569,8 @@ def run_gjp(args):
         result["kernels_phantom"] = phantom_kernels(args, gjp, geom, vg, cg, dev, stream, hbm, peak_kind, k16)
     if world == 1 and not args.no_batch and not args.first_views:
         name, make = BATCH_MIXES["small"]
-        ms, samples, _, _ = batch_measure(make(), args.warmup, max(1, min(args.steps, 10)), dev)
-        result["batching_small"] = {"workload": name, "samples": samples, **batch_summary(ms, samples)}
+        ms, counts, _, _ = batch_measure(make(), args.warmup, max(1, min(args.steps, 10)), dev)
+        result["batching_small"] = {"workload": name, "samples": counts[0], **batch_summary(ms, counts)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args, gjp, vg, cg, proj32, proj16)
         if "error_vs_oracle" in result["cpu_baseline"]:
@@ -934,7 +934,7 @@ def batch_measure(specs, warmup, steps, dev, clocks=False):
     clock record or None)."""
     import torch
     import paper_1609_00958_gb300 as gjp
-    items, samples = [], 0
+    items, samples, alg_bytes = [], 0, 0.0
     for sp in specs:
         vg, cg = sp.geometry()
         vol_np = (synth.voxelize(vg, supersample=2) if sp.content == "phantom"
@@ -943,6 +943,12 @@ def batch_measure(specs, warmup, steps, dev, clocks=False):
         g = gjp.Geometry.from_cone(cg)
         items.append((vol, g, vg.h, None, torch.empty(g.proj_shape, device=dev)))
         samples += int(sample_counts_device(vg, cg, dev).sum())
+        # compulsory bytes: the footprint of up to 16 evenly spaced views,
+        # scaled to all views, times the storage size, plus the projections
+        pick = sorted({int(round(k * cg.n_views / min(16, cg.n_views))) % cg.n_views
+                       for k in range(min(16, cg.n_views))})
+        foot = float(np.mean(gjp.footprint_voxels(g, vg.n, vg.h, views=pick, device=dev)))
+        alg_bytes += foot * cg.n_views * vol.element_size() + 4.0 * cg.n_views * cg.nu * cg.nv
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn, reps):
@@ -991,12 +997,17 @@ def batch_measure(specs, warmup, steps, dev, clocks=False):
         clk = c.summary()
     else:
         ms["batched_autotuned_graph"] = timed(graph.replay, steps)
-    return {k: round(v, 3) for k, v in ms.items()}, samples, tunings, clk
+    return {k: round(v, 3) for k, v in ms.items()}, (samples, alg_bytes), tunings, clk
 
 
-def batch_summary(ms, samples):
+def batch_summary(ms, counts):
+    samples, alg_bytes = counts
     gsps = lambda m: round(samples / (m * 1e-3) / 1e9, 2)
+    hbm, peak_kind = peaks()
+    best = ms["batched_autotuned_graph"]
     return {"ms": ms, "gsamples_s": {k: gsps(v) for k, v in ms.items()},
+            "algorithmic_gb": round(alg_bytes / 1e9, 3),
+            "frac_of_" + peak_kind + "_hbm": round(alg_bytes / (best * 1e-3) / 1e9 / hbm, 4),
             "speedup_vs_separate": round(ms["separate_launches"] / ms["batched_autotuned_graph"], 3),
             "speedup_vs_separate_graph": round(ms["separate_launches_graph"] / ms["batched_autotuned_graph"], 3),
             "speedup_vs_separate_4_streams": round(ms["separate_launches_4_streams"] / ms["batched_autotuned_graph"],
@@ -1024,8 +1035,9 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     name, make = BATCH_MIXES[args.batch_mix]
     specs = make()
-    ms, samples, tunings, clocks = batch_measure(specs, args.warmup, args.steps, dev, clocks=True)
-    out = batch_summary(ms, samples)
+    ms, counts, tunings, clocks = batch_measure(specs, args.warmup, args.steps, dev, clocks=True)
+    out = batch_summary(ms, counts)
+    samples = counts[0]
     print(json.dumps({
         "metric": METRIC + " (batching form)", "value": out["gsamples_s"]["batched_autotuned_graph"], "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["batched_autotuned_graph"],
