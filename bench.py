@@ -69,7 +69,7 @@ def parse_args(argv=None):
     p.add_argument("--views", type=int, default=360)
     p.add_argument("--first-views", type=int, default=0,
                    help="keep only the first K views of the --views geometry (small profiling captures)")
-    p.add_argument("--forward-path", choices=["auto", "gather", "slab", "prefetch", "texture", "hwlin"],
+    p.add_argument("--forward-path", choices=["auto", "gather", "pairs", "slab", "prefetch", "texture", "hwlin"],
                    default="auto", help="forward kernel family of the step (profiling other families)")
     p.add_argument("--tile-u", type=int, default=None, help="detector columns per block (library default if unset)")
     p.add_argument("--view-group", type=int, default=None, help="views issued together (library default if unset)")
@@ -556,13 +556,15 @@ def run_gjp(args):
         "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg_full.n_views,
                    "launch": {"tile_u": geom.launch[0], "view_group": geom.launch[1]},
                    "forward_path": args.forward_path,
+                   "tap_source": {"forward_f32": "volume", k16: "z-paired copy, written per call"
+                                  if launches_per_step(args.forward_path, vg.n) > 3 else "volume"},
                    "step": "forward f32 + forward bf16 + adjoint f32", "samples_per_kernel": samples_per_kernel,
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "one GPU" if world == 1 else
                    f"one scan split by views over {world} GPUs (rank views {scan.start}..{scan.stop - 1}), "
                    "adjoint volumes summed by one all-reduce"},
         "kernels": kernels, "roofline": roofline, "clocks": clocks,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": launches_per_step(args.forward_path, vg.n) * args.steps,
         "e2e": e2e,
     }
     if world == 1 and args.content == "random" and not args.no_phantom and not args.first_views:
@@ -580,6 +582,16 @@ def run_gjp(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def launches_per_step(path: str, n) -> int:
+    """The library's kernel launches in one step: forward f32, forward bf16
+    and the adjoint, plus the z-paired copy that a "pairs" forward writes
+    first (AUTO takes it for 16-bit storage; both only where the element
+    offsets fit 32 bits, the library's fits_int32 rule)."""
+    nx, ny, nz = (int(v) for v in n)
+    fits = nx * ny * nz + 2 * (ny * nz + nz + 1) < 2147483647
+    return 3 + int(fits and path in ("auto", "pairs")) + int(fits and path == "pairs")
 
 
 def phantom_kernels(args, gjp, geom, vg, cg, dev, stream, hbm, peak_kind, k16):

@@ -164,8 +164,9 @@ gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_
 
 /* Kernel family used by gjp_forward_ex. */
 typedef enum {
-    GJP_PATH_AUTO = 0,   /* the library's fastest family for the call (forward: GATHER,
-                            adjoint: COMBINE) */
+    GJP_PATH_AUTO = 0,   /* the library's fastest family for the call (forward: PAIRS for
+                            16-bit storage where it applies, else GATHER; adjoint:
+                            COMBINE) */
     GJP_PATH_GATHER = 1, /* one thread per ray, taps gathered from global memory */
     GJP_PATH_SLAB = 2,   /* detector tiles stream per-plane voxel boxes into shared memory
                             with TMA; needs a 16-byte aligned volume whose z row is a
@@ -177,9 +178,11 @@ typedef enum {
     GJP_PATH_TEXTURE = 5, /* forward only, float32 / float16 volumes: the four taps of a
                             sample come from one texture gather (tld4) on a layered copy of
                             the volume; exact float32 weights (see below) */
-    GJP_PATH_HWLIN = 6    /* forward only, float32 / float16 volumes, w_lin: GJP_hwlin, one
+    GJP_PATH_HWLIN = 6,   /* forward only, float32 / float16 volumes, w_lin: GJP_hwlin, one
                             hardware-filtered 3-D texture fetch per sample; the hardware
                             quantises the interpolation weights to 1/256 (see below) */
+    GJP_PATH_PAIRS = 7    /* forward only: GATHER, with the row-table march reading a
+                            z-paired copy of the volume (see below) */
 } gjp_path;
 
 /*
@@ -201,6 +204,23 @@ typedef enum {
  * GPU (they share the arrays).  HWLIN's 1/256 weight steps put its error
  * near 1e-4 .. 1e-3 of the projection maximum: above the float32 parity
  * bound, so GJP_PATH_AUTO never takes it.
+ *
+ * PAIRS first writes a z-paired copy of the volume, whose element e holds
+ * voxels e and e + 1 of the same z line (the upper one zero past the last
+ * z), and the row-table march of GATHER then reads both z taps of a row with
+ * one aligned load (8 bytes for float32, 4 for 16-bit storage) instead of
+ * two; every other part of GATHER is unchanged and the results are bitwise
+ * equal to GATHER's.  The copy (8 or 4 bytes per voxel) is allocated on
+ * `stream` from a memory pool of the library and released on `stream`
+ * after the projection; the pool keeps up to 8 GiB for later calls (see
+ * gjp_trim_workspace).  PAIRS returns GJP_ERR_UNSUPPORTED while `stream`
+ * is being captured into a CUDA graph and for grids whose element offsets
+ * do not fit 32 bits, and GJP_ERR_OOM when the copy cannot be allocated.
+ * GJP_PATH_AUTO takes PAIRS for bfloat16 and float16 storage (measured
+ * faster than GATHER: half the load instructions, same L1 lines per load)
+ * and falls back to GATHER wherever PAIRS returns one of those statuses;
+ * for float32 it takes GATHER (the 8-byte copy doubles the footprint in the
+ * caches and measured slower).
  */
 gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
                           const double voxel_size[3], const double volume_origin[3],
@@ -245,13 +265,24 @@ gjp_status gjp_selftest_tap_check(void *stream);
 /*
  * gjp_debug_fail_allocations -- failure-injection hook for tests (the paper
  * has no counterpart): the next `n` device allocations that the library
- * attempts (per-view tables, batch queues, texture arrays) fail as if the
- * device were out of memory, so the calls that need them return
- * GJP_ERR_OOM and leave their outputs untouched; later allocations proceed.
+ * attempts (per-view tables, batch queues, texture arrays, z-paired
+ * copies) fail as if the device were out of memory, so the calls that need
+ * them return GJP_ERR_OOM and leave their outputs untouched (GJP_PATH_AUTO
+ * reads the volume directly instead of a z-paired copy it could not
+ * allocate); later allocations proceed.
  * n = 0 clears it.  Host-only, thread-safe; no GPU fault is involved.
  * Returns GJP_ERR_INVALID_ARG for n < 0.
  */
 gjp_status gjp_debug_fail_allocations(int n);
+
+/*
+ * gjp_trim_workspace -- returns to the device the memory that the
+ * library's workspace pools keep between calls (the z-paired copies of
+ * GJP_PATH_PAIRS; up to 8 GiB per device).  Waits for nothing: memory that
+ * a queued call still uses is kept until that call is done.  Safe to call
+ * at any time; GJP_OK unless CUDA reports an error.
+ */
+gjp_status gjp_trim_workspace(void);
 
 /*
  * gjp_adjoint -- matched transpose of gjp_forward (float32 volume):

@@ -16,7 +16,7 @@ import numpy as np
 from . import _capi, tuning_cache
 from ._capi import GjpError
 
-__all__ = ["Geometry", "Batch", "forward", "adjoint", "footprint_voxels", "stream_status", "GjpError",
+__all__ = ["Geometry", "Batch", "forward", "adjoint", "footprint_voxels", "stream_status", "trim_workspace", "GjpError",
            "library_path"]
 
 
@@ -121,7 +121,8 @@ def _stream(t, stream):
     return int(stream.cuda_stream)
 
 
-_PATHS = {"auto": 0, "gather": 1, "slab": 2, "prefetch": 3, "combine": 4, "texture": 5, "hwlin": 6}
+_PATHS = {"auto": 0, "gather": 1, "slab": 2, "prefetch": 3, "combine": 4, "texture": 5, "hwlin": 6,
+          "pairs": 7}
 
 
 def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None, out=None, stream=None,
@@ -129,7 +130,8 @@ def forward(volume, geometry: Geometry, voxel_size=(1.0, 1.0, 1.0), origin=None,
     """GJP forward projection (Algorithm 1) of a ``(nx, ny, nz)`` CUDA
     volume (float32, bfloat16 or float16 storage) into ``(n_views, nv, nu)``
     float32 projections.  ``path`` selects the kernel family ("auto",
-    "gather" or "slab"; see ``gjp_forward_ex``)."""
+    "gather", "pairs", "slab", "prefetch", "texture" or "hwlin"; see
+    ``gjp_forward_ex``)."""
     torch = _torch()
     _check_cuda(volume, "volume")
     if volume.dim() != 3:
@@ -191,6 +193,14 @@ def footprint_voxels(geometry: Geometry, shape, voxel_size=(1.0, 1.0, 1.0), orig
                 raise GjpError(st, "gjp_footprint")
             counts.append(torch.count_nonzero(marks))
     return [int(c.item()) for c in counts]
+
+
+def trim_workspace():
+    """Returns to the device the memory the library keeps between calls for
+    the z-paired copies of the "pairs" forward (``gjp_trim_workspace``)."""
+    st = _capi.gjp_trim_workspace()
+    if st != _capi.GJP_OK:
+        raise GjpError(st, "gjp_trim_workspace")
 
 
 def stream_status(stream=None):

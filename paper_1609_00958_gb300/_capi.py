@@ -36,12 +36,13 @@ GJP_PATH_PREFETCH = 3
 GJP_PATH_COMBINE = 4
 GJP_PATH_TEXTURE = 5
 GJP_PATH_HWLIN = 6
+GJP_PATH_PAIRS = 7
 
 #: every symbol include/gjp.h declares
 EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "gjp_geometry_set_weight",
            "gjp_geometry_set_launch", "gjp_geometry_get_launch", "gjp_geometry_set_fov", "gjp_forward",
            "gjp_forward_ex", "gjp_forward_noalloc", "gjp_stream_status", "gjp_selftest_wait_timeout",
-           "gjp_selftest_tap_check", "gjp_debug_fail_allocations", "gjp_adjoint", "gjp_adjoint_ex",
+           "gjp_selftest_tap_check", "gjp_debug_fail_allocations", "gjp_trim_workspace", "gjp_adjoint", "gjp_adjoint_ex",
            "gjp_footprint", "gjp_batch_create", "gjp_batch_destroy", "gjp_batch_forward",
            "gjp_batch_autotune", "gjp_batch_get_tuning", "gjp_batch_set_tuning", "gjp_status_string")
 
@@ -106,6 +107,8 @@ def load(path: str | None = None):
     lib.gjp_selftest_tap_check.restype = _I
     lib.gjp_debug_fail_allocations.argtypes = [_I]
     lib.gjp_debug_fail_allocations.restype = _I
+    lib.gjp_trim_workspace.argtypes = []
+    lib.gjp_trim_workspace.restype = _I
     lib.gjp_adjoint.argtypes = [_P, _P, _I64, _I64, _I64, _D3, _D3, _P, _I, _P]
     lib.gjp_adjoint.restype = _I
     lib.gjp_adjoint_ex.argtypes = [_P, _P, _I64, _I64, _I64, _D3, _D3, _P, _I, _I, _P]
@@ -227,6 +230,10 @@ def gjp_selftest_tap_check(stream: int) -> int:
 
 def gjp_debug_fail_allocations(n: int) -> int:
     return load().gjp_debug_fail_allocations(int(n))
+
+
+def gjp_trim_workspace() -> int:
+    return load().gjp_trim_workspace()
 
 
 def gjp_adjoint(d_proj: int, geometry, nx: int, ny: int, nz: int, voxel_size, volume_origin,

@@ -49,6 +49,61 @@ bool alloc_gate()
     return true;
 }
 
+// Stream-ordered workspace of the z-paired copy: one memory pool per
+// device, owned by the library.  It keeps up to kPairsKeep bytes across
+// synchronisations, so that repeated calls on grids up to that size reuse
+// their memory instead of mapping it again; larger copies are returned to
+// the device at the next synchronisation.
+constexpr unsigned long long kPairsKeep = 8ull << 30;
+std::mutex g_pairs_mu;
+std::vector<std::pair<int, cudaMemPool_t>> g_pairs_pools;
+
+cudaMemPool_t pairs_pool(int dev)
+{
+    std::lock_guard<std::mutex> lock(g_pairs_mu);
+    for (const auto &p : g_pairs_pools)
+        if (p.first == dev) return p.second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    unsigned long long keep = kPairsKeep;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pairs_pools.emplace_back(dev, pool);
+    return pool;
+}
+
+// Allocates `bytes` on stream s for the z-paired copy.  GJP_ERR_UNSUPPORTED
+// while s is being captured into a graph (the copy would become a graph
+// allocation); GJP_ERR_OOM when the allocation gate refuses or the device
+// has no room (the CUDA error is cleared).
+gjp_status pairs_alloc(size_t bytes, cudaStream_t s, void **out)
+{
+    *out = nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return GJP_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return GJP_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GJP_ERR_CUDA;
+    cudaMemPool_t pool = pairs_pool(dev);
+    if (!pool) return GJP_ERR_CUDA;
+    if (!alloc_gate()) return GJP_ERR_OOM;
+    if (cudaMallocFromPoolAsync(out, bytes, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return GJP_ERR_OOM;
+    }
+    return GJP_OK;
+}
+
 void split(double x, float &hi, float &lo)
 {
     hi = (float)x;
@@ -167,10 +222,11 @@ gjp_status get_table(const gjp_geometry *gc, const int64_t n[3], const double h[
     return GJP_OK;
 }
 
-template <typename T, typename Index, bool SPL>
+template <typename T, typename Index, bool SPL, bool PAIRS>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksMax) gjp_forward_kernel(
     const T *__restrict__ vol, VolParams V, const ViewParams *__restrict__ views,
-    int nu, int nv, int n_tv, int n_views, int view_group, float *__restrict__ proj)
+    int nu, int nv, int n_tv, int n_views, int view_group, float *__restrict__ proj,
+    const typename PairOf<T>::type *__restrict__ pairs)
 {
     int tile, view;
     block_tile_view(n_views, view_group, tile, view);
@@ -179,7 +235,28 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocksMax) gjp_forward_kernel
     const unsigned act = __ballot_sync(0xffffffffu, iv < nv && iu < nu);
     if (iv >= nv || iu >= nu) return;
     proj[((size_t)view * nv + iv) * nu + iu] =
-        forward_ray<T, Index, SPL>(vol, V, views + view, nu, nv, iu, iv, act, (int)threadIdx.y);
+        forward_ray<T, Index, SPL, PAIRS>(vol, V, views + view, nu, nv, iu, iv, act, (int)threadIdx.y, pairs);
+}
+
+// The z-paired copy of a volume (read by the row-table march): element e
+// holds voxels e and e + 1 of its z line, the upper one zero at the last z.
+// One block per z line at a time; consecutive threads take consecutive z.
+template <typename T>
+__global__ void gjp_zpairs_kernel(const T *__restrict__ vol, long long lines, int nz,
+                                  typename PairOf<T>::type *__restrict__ out)
+{
+    using W = typename Raw<T>::type;
+    for (long long r = blockIdx.x; r < lines; r += gridDim.x) {
+        const T *line = vol + r * nz;
+        typename PairOf<T>::type *o = out + r * nz;
+        for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+            const W lo = load_raw(line + z), hi = z + 1 < nz ? load_raw(line + z + 1) : W(0);
+            if constexpr (std::is_same<T, float>::value)
+                o[z] = make_float2(lo, hi);
+            else
+                o[z] = (unsigned)lo | ((unsigned)hi << 16);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1475,9 +1552,11 @@ cudaError_t launch_gather_pf(const T *vol, gjp_dtype dt, const int64_t n[3], con
     return cudaGetLastError();
 }
 
+// pairs: the z-paired copy of vol for the row-table march (32-bit offsets
+// only), or null to read the taps from vol.
 template <typename T>
 cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *table, const gjp_geometry &g,
-                          bool i32, float *proj, cudaStream_t s)
+                          bool i32, float *proj, cudaStream_t s, const typename PairOf<T>::type *pairs = nullptr)
 {
     const int n_tv = (g.nv + kTileV - 1) / kTileV;
     const int n_tu = (g.nu + g.tile_u - 1) / g.tile_u;
@@ -1486,17 +1565,33 @@ cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *ta
     const bool spl = g.weight == GJP_WEIGHT_SPL;
     const int nvw = g.n_views, vgp = launch_view_group(g, V.n);
     const size_t rows = (size_t)g.tile_u * 32 * sizeof(uint2);   // row tables (32-bit offsets only)
-    if (i32) {
-        if (spl)
-            gjp_forward_kernel<T, int, true><<<grid, block, rows, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
-        else
-            gjp_forward_kernel<T, int, false><<<grid, block, rows, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
+#define GJP_LAUNCH_FWD(I, S, P, SMEM)                                                                              \
+    gjp_forward_kernel<T, I, S, P><<<grid, block, SMEM, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj, pairs)
+    if (i32 && pairs) {
+        if (spl) GJP_LAUNCH_FWD(int, true, true, rows);
+        else GJP_LAUNCH_FWD(int, false, true, rows);
+    } else if (i32) {
+        if (spl) GJP_LAUNCH_FWD(int, true, false, rows);
+        else GJP_LAUNCH_FWD(int, false, false, rows);
     } else {
-        if (spl)
-            gjp_forward_kernel<T, long long, true><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
-        else
-            gjp_forward_kernel<T, long long, false><<<grid, block, 0, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj);
+        if (spl) GJP_LAUNCH_FWD(long long, true, false, 0);
+        else GJP_LAUNCH_FWD(long long, false, false, 0);
     }
+#undef GJP_LAUNCH_FWD
+    return cudaGetLastError();
+}
+
+// Writes the z-paired copy of vol (n[0] n[1] lines of n[2] voxels) to out.
+template <typename T>
+cudaError_t launch_zpairs(const T *vol, const int64_t n[3], typename PairOf<T>::type *out, cudaStream_t s)
+{
+    const long long lines = (long long)n[0] * n[1];
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = n[2] >= 256 ? 256 : 128;
+    const long long blocks = std::min<long long>(lines, (long long)std::max(sms, 1) * 8);
+    gjp_zpairs_kernel<T><<<(unsigned)blocks, threads, 0, s>>>(vol, lines, (int)n[2], out);
     return cudaGetLastError();
 }
 
@@ -1541,6 +1636,27 @@ gjp_status forward_typed(const void *d_volume, gjp_dtype dt, const int64_t n[3],
             return e == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
         }
         if (path == GJP_PATH_SLAB) return GJP_ERR_UNSUPPORTED;
+    }
+    // The z-paired copy: on request (PAIRS), and taken by AUTO for 16-bit
+    // storage when the offsets fit 32 bits and the copy can be allocated
+    // (otherwise AUTO reads the volume directly).  Its results are bitwise
+    // those of GATHER.  Measured on the 512^3 / 360-view workload it makes
+    // the 16-bit forward 11% faster (copy included) and the float32 one 35%
+    // slower (8-byte words: twice the footprint in L1 and L2).
+    constexpr bool kPairsAuto = !std::is_same<T, float>::value;
+    if (path == GJP_PATH_PAIRS || (path == GJP_PATH_AUTO && kPairsAuto && i32)) {
+        if (!i32) return GJP_ERR_UNSUPPORTED;
+        using P = typename PairOf<T>::type;
+        void *ws = nullptr;
+        const gjp_status st = pairs_alloc((size_t)(n[0] * n[1] * n[2]) * sizeof(P), s, &ws);
+        if (st == GJP_OK) {
+            P *pairs = static_cast<P *>(ws);
+            cudaError_t e = launch_zpairs<T>(vol, n, pairs, s);
+            if (e == cudaSuccess) e = launch_gather<T>(vol, V, table, g, i32, proj, s, pairs);
+            const cudaError_t f = cudaFreeAsync(pairs, s);
+            return e == cudaSuccess && f == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+        }
+        if (path == GJP_PATH_PAIRS || st == GJP_ERR_CUDA) return st;
     }
     return launch_gather<T>(vol, V, table, g, i32, proj, s) == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
 }
@@ -1776,7 +1892,7 @@ gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int
     if (!d_volume || !g || !d_proj) return GJP_ERR_INVALID_ARG;
     if (dtype != GJP_F32 && dtype != GJP_BF16 && dtype != GJP_F16) return GJP_ERR_INVALID_ARG;
     if (path != GJP_PATH_AUTO && path != GJP_PATH_GATHER && path != GJP_PATH_SLAB && path != GJP_PATH_PREFETCH &&
-        path != GJP_PATH_TEXTURE && path != GJP_PATH_HWLIN)
+        path != GJP_PATH_TEXTURE && path != GJP_PATH_HWLIN && path != GJP_PATH_PAIRS)
         return GJP_ERR_INVALID_ARG;
     int64_t n[3];
     double h[3], o[3];
@@ -1855,6 +1971,14 @@ gjp_status gjp_debug_fail_allocations(int n)
 {
     if (n < 0) return GJP_ERR_INVALID_ARG;
     g_fail_allocations.store(n);
+    return GJP_OK;
+}
+
+gjp_status gjp_trim_workspace(void)
+{
+    std::lock_guard<std::mutex> lock(g_pairs_mu);
+    for (const auto &p : g_pairs_pools)
+        if (cudaMemPoolTrimTo(p.second, 0) != cudaSuccess) return GJP_ERR_CUDA;
     return GJP_OK;
 }
 

@@ -358,6 +358,53 @@ __device__ __forceinline__ float2 eq12_pair(typename Raw<T>::type v00x, typename
 }
 
 // ---------------------------------------------------------------------------
+// The two z taps (z, z + 1) of one transverse row.  The row-table march
+// reads them either from the volume itself (two loads) or from a z-paired
+// copy of it, whose element e holds voxels e and e + 1 of the same z line
+// (the upper one zero past the last z): one aligned 8-byte (float32) or
+// 4-byte (16-bit) load then brings both taps, which halves the march's load
+// instructions and, for 16-bit storage, its L1 wavefronts.  Both sources
+// give the same tap values, so the results are bitwise equal.
+
+template <typename T> struct PairOf { using type = float2; };
+template <> struct PairOf<__nv_bfloat16> { using type = unsigned; };
+template <> struct PairOf<__half> { using type = unsigned; };
+
+template <typename T> struct ZTaps { typename Raw<T>::type lo, hi; };
+
+template <typename T> __device__ __forceinline__ ZTaps<T> load_zrow(const T *p) { return {load_raw(p), load_raw(p + 1)}; }
+__device__ __forceinline__ float2 load_zrow(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ unsigned load_zrow(const unsigned *p) { return __ldg(p); }
+
+// the row's taps by source word: ZTaps<T> (plain), float2 or unsigned (paired)
+template <typename T, typename Z> __device__ __forceinline__ void split_zrow(Z r, typename Raw<T>::type &lo,
+                                                                             typename Raw<T>::type &hi)
+{
+    if constexpr (std::is_same<Z, ZTaps<T>>::value) {
+        lo = r.lo;
+        hi = r.hi;
+    } else if constexpr (std::is_same<Z, float2>::value) {
+        lo = r.x;
+        hi = r.y;
+    } else {
+        asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(r));
+    }
+}
+
+// Two samples of Eq. 12 from their rows' z-tap words: r0 (lower transverse
+// row) and r1 (upper row) of samples x and y.
+template <typename T, typename Z>
+__device__ __forceinline__ float2 eq12_rows(Z r0x, Z r0y, Z r1x, Z r1y, float2 da, float2 db)
+{
+    typename Raw<T>::type v00x, v01x, v00y, v01y, v10x, v11x, v10y, v11y;
+    split_zrow<T>(r0x, v00x, v01x);
+    split_zrow<T>(r0y, v00y, v01y);
+    split_zrow<T>(r1x, v10x, v11x);
+    split_zrow<T>(r1y, v10y, v11y);
+    return eq12_pair<T>(v00x, v00y, v01x, v01y, v10x, v10y, v11x, v11y, da, db);
+}
+
+// ---------------------------------------------------------------------------
 // Per-ray setup.
 
 struct Ray {
@@ -727,24 +774,25 @@ __device__ __forceinline__ float march_boundary(const T *__restrict__ vol, const
 
 // One 16-plane block of the row-table march (below): e holds, per pair of
 // planes (t, t + 1), the words (row weight t, row weight t + 1, row offset
-// t, row offset t + 1), read with one 16-byte load; pb steps along z.
-// CHECKED loads only the taps of planes 0 <= d + t < cnt (this lane's
-// interior), the others contribute zero, and stops after `n` planes
+// t, row offset t + 1), read with one 16-byte load; pb steps along z.  src
+// is the volume (S = T) or its z-paired copy (S = PairOf<T>::type), indexed
+// alike.  CHECKED loads only the taps of planes 0 <= d + t < cnt (this
+// lane's interior), the others contribute zero, and stops after `n` planes
 // (warp-uniform: no lane has an interior plane past them).  Returns the
 // block sum as an FP32 pair (even and odd planes).
-template <typename T, bool SPL, bool CHECKED>
-__device__ __forceinline__ float2 rows_block(const T *__restrict__ vol, const uint4 *__restrict__ e,
+template <typename T, bool SPL, bool CHECKED, typename S>
+__device__ __forceinline__ float2 rows_block(const S *__restrict__ src, const uint4 *__restrict__ e,
                                              unsigned long long &pb, unsigned long long gb, int sa, int d, int cnt,
                                              int n, int ip, int dir, const Ray &R)
 {
     // (ip, dir: plane index of entry 0 and the march direction, for the
     // tap check of the debug build)
-    using W = typename Raw<T>::type;
+    using Z = decltype(load_zrow(src));
     float2 blk = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         if (CHECKED && q * kBatch >= n) break;
-        W v00[kBatch], v01[kBatch], v10[kBatch], v11[kBatch];
+        Z r0[kBatch], r1[kBatch];                    // lower / upper transverse row
         unsigned long long qb[kBatch];
         float2 da[kBatch / 2];
         unsigned off[kBatch];
@@ -758,29 +806,19 @@ __device__ __forceinline__ float2 rows_block(const T *__restrict__ vol, const ui
 #pragma unroll
         for (int t = 0; t < kBatch; ++t) {
             qb[t] = pb;
-            const T *p = vol + (int)(off[t] + (unsigned)floor_of(pb));
+            const S *p = src + (int)(off[t] + (unsigned)floor_of(pb));
             const int i = ip + dir * (q * kBatch + t);
-            if (CHECKED) {
-                const bool in = (unsigned)(d + q * kBatch + t) < (unsigned)cnt &&
-                                (!GJP_CHECK_TAPS || row_taps_in_grid(off[t], i, floor_of(pb), R));
-                v00[t] = in ? load_raw(p) : W(0);
-                v01[t] = in ? load_raw(p + 1) : W(0);
-                v10[t] = in ? load_raw(p + sa) : W(0);
-                v11[t] = in ? load_raw(p + sa + 1) : W(0);
-            } else {
-                const bool ok = row_taps_in_grid(off[t], i, floor_of(pb), R);   // debug build only
-                v00[t] = ok ? load_raw(p) : W(0);
-                v01[t] = ok ? load_raw(p + 1) : W(0);
-                v10[t] = ok ? load_raw(p + sa) : W(0);
-                v11[t] = ok ? load_raw(p + sa + 1) : W(0);
-            }
+            const bool in = CHECKED ? (unsigned)(d + q * kBatch + t) < (unsigned)cnt &&
+                                          (!GJP_CHECK_TAPS || row_taps_in_grid(off[t], i, floor_of(pb), R))
+                                    : row_taps_in_grid(off[t], i, floor_of(pb), R);   // debug build only
+            r0[t] = in ? load_zrow(p) : Z{};
+            r1[t] = in ? load_zrow(p + sa) : Z{};
             pb += gb;
         }
 #pragma unroll
         for (int t = 0; t < kBatch; t += 2) {
             const float2 db = upper_weight2<SPL>(qb[t], qb[t + 1]);
-            blk = __fadd2_rn(blk, eq12_pair<T>(v00[t], v00[t + 1], v01[t], v01[t + 1], v10[t], v10[t + 1], v11[t],
-                                               v11[t + 1], da[t / 2], db));
+            blk = __fadd2_rn(blk, eq12_rows<T>(r0[t], r0[t + 1], r1[t], r1[t + 1], da[t / 2], db));
         }
     }
     return blk;
@@ -800,8 +838,8 @@ __device__ __forceinline__ float2 rows_block(const T *__restrict__ vol, const ui
 // `rows` is this warp's 32-entry table (256 bytes, 16-byte aligned): per
 // pair of planes the row weight bits of both, then the row offsets of both
 // (the layout rows_block reads).
-template <typename T, bool SPL>
-__device__ __forceinline__ float march_interior_rows(const T *__restrict__ vol, const Ray &R, bool rev,
+template <typename T, bool SPL, typename S>
+__device__ __forceinline__ float march_interior_rows(const S *__restrict__ src, const Ray &R, bool rev,
                                                      uint4 *__restrict__ rows, int lane)
 {
     const unsigned full = 0xffffffffu;
@@ -841,9 +879,9 @@ __device__ __forceinline__ float march_interior_rows(const T *__restrict__ vol, 
             const int k = w + kb;
             const int ip = i0 + dir * k;
             if (k >= K0 && k + 15 <= K1)              // warp-uniform
-                acc = __fadd2_rn(acc, rows_block<T, SPL, false>(vol, rows + kb / 2, pb, gb, sa, 0, 0, 16, ip, dir, R));
+                acc = __fadd2_rn(acc, rows_block<T, SPL, false>(src, rows + kb / 2, pb, gb, sa, 0, 0, 16, ip, dir, R));
             else
-                acc = __fadd2_rn(acc, rows_block<T, SPL, true>(vol, rows + kb / 2, pb, gb, sa, k - k_lo, cnt, L - k,
+                acc = __fadd2_rn(acc, rows_block<T, SPL, true>(src, rows + kb / 2, pb, gb, sa, k - k_lo, cnt, L - k,
                                                                ip, dir, R));
         }
     }
@@ -868,11 +906,13 @@ __device__ __forceinline__ int lane_id()
 // GJP line integral of the ray through detector pixel (iu, iv) of the view
 // whose table entry is *view (Algorithm 1).  Called by every lane of the
 // warp set in `act` (the lanes that hold a ray; they share the warp-level
-// choice of march direction).
-template <typename T, typename Index, bool SPL>
+// choice of march direction).  PAIRS: the row-table march reads its taps
+// from `pairs`, the z-paired copy of vol (32-bit offsets only).
+template <typename T, typename Index, bool SPL, bool PAIRS = false>
 __device__ __forceinline__ float forward_ray(const T *__restrict__ vol, const VolParams &V,
                                              const ViewParams *__restrict__ view, int nu, int nv, int iu, int iv,
-                                             unsigned act, int rows_slot = -1)
+                                             unsigned act, int rows_slot = -1,
+                                             const typename PairOf<T>::type *__restrict__ pairs = nullptr)
 {
     ViewParams vp;
     load_view(view, 0, vp);
@@ -891,14 +931,18 @@ __device__ __forceinline__ float forward_ray(const T *__restrict__ vol, const Vo
     // the few boundary planes first: afterwards only the interior march's
     // state stays live, which keeps the unrolled loop within the register budget
     const float bsum = march_boundary<T, Index, SPL>(vol, R);
+    static_assert(!PAIRS || std::is_same<Index, int>::value, "the z-paired copy is read with 32-bit offsets");
     if constexpr (std::is_same<Index, int>::value) {
         // a full warp with one common row: the shared row table
         if (GJP_ROWS && rows_slot >= 0 && act == 0xffffffffu) {
             const int m0 = __shfl_sync(act, R.m, 0);
             const long long Pa0 = __shfl_sync(act, R.Pa, 0), Ga0 = __shfl_sync(act, R.Ga, 0);
-            if (__all_sync(act, R.m == m0 && R.Pa == Pa0 && R.Ga == Ga0) && m0 != 2)
-                return (march_interior_rows<T, SPL>(vol, R, rev, gjp_row_tables + 16 * rows_slot, lane_id()) + bsum) *
-                       R.step;
+            if (__all_sync(act, R.m == m0 && R.Pa == Pa0 && R.Ga == Ga0) && m0 != 2) {
+                uint4 *rows = gjp_row_tables + 16 * rows_slot;
+                const float acc = PAIRS ? march_interior_rows<T, SPL>(pairs, R, rev, rows, lane_id())
+                                        : march_interior_rows<T, SPL>(vol, R, rev, rows, lane_id());
+                return (acc + bsum) * R.step;
+            }
         }
     }
     const float acc = (R.m != 2) ? march_interior<T, Index, true, SPL>(vol, R, rev)

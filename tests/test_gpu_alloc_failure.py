@@ -91,3 +91,26 @@ def test_texture_array_allocation_failure(gjp, capi):
     out = gjp.forward(vol, g2, vg.h, path="texture")
     gjp.stream_status()
     assert torch.equal(out, ref)
+
+
+def test_pairs_copy_allocation_failure(gjp, capi):
+    """AUTO reads the volume directly when the z-paired copy of a 16-bit
+    volume cannot be allocated; an explicit "pairs" call reports it."""
+    vg, cg, vol = _case()
+    g = gjp.Geometry.from_cone(cg)
+    v16 = vol.to(torch.bfloat16)
+    ref = gjp.forward(v16, g, vg.h, path="gather")   # the table exists from here on
+    capi.gjp_debug_fail_allocations(1)
+    got = gjp.forward(v16, g, vg.h)
+    gjp.stream_status()
+    assert torch.equal(got, ref)
+    out = torch.full(g.proj_shape, 7.0, device="cuda")
+    capi.gjp_debug_fail_allocations(1)
+    with pytest.raises(gjp.GjpError) as e:
+        gjp.forward(v16, g, vg.h, out=out, path="pairs")
+    assert e.value.status == capi.GJP_ERR_OOM
+    torch.cuda.synchronize()
+    assert bool((out == 7.0).all())
+    gjp.forward(v16, g, vg.h, out=out, path="pairs")
+    gjp.stream_status()
+    assert torch.equal(out, ref)
