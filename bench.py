@@ -71,6 +71,9 @@ def parse_args(argv=None):
                    help="keep only the first K views of the --views geometry (small profiling captures)")
     p.add_argument("--forward-path", choices=["auto", "gather", "pairs", "slab", "prefetch", "texture", "hwlin"],
                    default="auto", help="forward kernel family of the step (profiling other families)")
+    p.add_argument("--path16", choices=["gather", "pairs"], default=None,
+                   help="forward family of the 16-bit forward only (default: --forward-path); a capture of the "
+                        "first views of a many-view scan uses it to run the family AUTO takes for the whole scan")
     p.add_argument("--tile-u", type=int, default=None, help="detector columns per block (library default if unset)")
     p.add_argument("--view-group", type=int, default=None, help="views issued together (library default if unset)")
     p.add_argument("--content", choices=["random", "phantom"], default="random")
@@ -286,11 +289,14 @@ _UNIT_SCALE = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1
 # touches two transverse rows over the z-span of 32 neighbouring rays, 33 voxels
 # (132 bytes in float32: two 128-byte L1 lines and five 32-byte sectors; 66 bytes in
 # 16-bit storage: one or two lines, 1.5 on average).
+# A note names the binding resource where the unit's own fraction is not the largest.
 LIMIT_MODEL = {
-    "gjp_forward_kernel<float": ("l1_wavefronts", "l1_wavefronts_pct", "L1 data-pipe wavefronts", 2 * 2.0),
+    "gjp_forward_kernel<float": ("l1_wavefronts", "l1_wavefronts_pct", "L1 data-pipe wavefronts", 2 * 2.0, None),
     "gjp_forward_kernel<__nv_bfloat16": ("l1_wavefronts", "l1_wavefronts_pct", "L1 data-pipe wavefronts",
-                                         2 * 1.5),
-    "gjp_adjoint_combine_kernel<int": ("l2_red_sectors", "l2_red_pct", "L2 reduction sectors", 2 * 5.0),
+                                         2 * 1.5, "z-paired taps: one 4-byte load per row; the L1 does not "
+                                         "saturate, issue slots and load latency (long-scoreboard stalls) bind"),
+    "gjp_adjoint_combine_kernel<int": ("l2_red_sectors", "l2_red_pct", "L2 reduction sectors", 2 * 5.0,
+                                       "issue slots bind first, the L2 reduction units next"),
 }
 
 
@@ -298,8 +304,9 @@ def kernel_key(name: str) -> str:
     """``gjp_forward_kernel<float`` from an ncu kernel name such as
     ``void gjp_detail::gjp_forward_kernel<float, int, 0>(const T1 *, ...)``."""
     import re
-    m = re.search(r"(\w+<[^,>(]+)", name.split("(")[0].replace("void ", ""))
-    return m.group(1) if m else name
+    base = name.split("(")[0].replace("void ", "").strip()
+    m = re.search(r"(\w+<[^,>(]+)", base)
+    return m.group(1) if m else base
 
 
 def _sources_hash():
@@ -330,11 +337,13 @@ def ncu_summary(csv_path: str, views: int, command: str, n: int = 512, n_views: 
         kernels.setdefault(key, {})[NCU_FIELDS[r[mi]]] = val   # the last launch of a kernel wins
     vg, cg = synth.scaled_c2_geometry(n, n, n_views, 10.0)
     samples = int(sample_counts(vg, cg.subset(range(views))).sum())
-    for e in kernels.values():
+    for key, e in kernels.items():
+        once = key.startswith("gjp_zpairs")              # once per forward call, whatever the view count
         if "dram_read_bytes" in e and "dram_write_bytes" in e:
             e["dram_bytes"] = e["dram_read_bytes"] + e["dram_write_bytes"]
-            e["bytes_per_launch"] = e["dram_bytes"] * n_views / views
-        e["samples_captured"] = samples
+            e["bytes_per_launch"] = e["dram_bytes"] * (1.0 if once else n_views / views)
+        if not once:
+            e["samples_captured"] = samples
     return {"sources": _sources_hash(), "kernels": kernels,
             "capture": {"views": views, "of_views": n_views, "volume": n, "command": command,
                         "note": f"one ncu capture of the first {views} views (one view group) of the {n_views}-view "
@@ -382,14 +391,17 @@ def limiter(kernel: str):
     model = LIMIT_MODEL.get(kernel)
     if e is None or model is None:
         return None
-    field, pct_field, unit, min_per_warp_plane = model
+    field, pct_field, unit, min_per_warp_plane, note = model
     try:
         per_sample = e[field] / e["samples_captured"]
         least = min_per_warp_plane / 32.0
-        return {"unit": unit, "pct_of_peak": round(e[pct_field], 2), "per_sample": round(per_sample, 4),
-                "min_per_sample": round(least, 4), "efficiency": round(least / per_sample, 3),
-                "issue_pct": round(e.get("issue_pct", float("nan")), 2),
-                "source": COUNTERS}
+        out = {"unit": unit, "pct_of_peak": round(e[pct_field], 2), "per_sample": round(per_sample, 4),
+               "min_per_sample": round(least, 4), "efficiency": round(least / per_sample, 3),
+               "issue_pct": round(e.get("issue_pct", float("nan")), 2),
+               "source": COUNTERS}
+        if note:
+            out["note"] = note
+        return out
     except (KeyError, TypeError, ZeroDivisionError):
         return None
 
@@ -482,7 +494,7 @@ def run_gjp(args):
         gjp.forward(v32, geom, vg.h, out=proj32, path=args.forward_path)
         if ev is not None:
             ev[1].record(stream)
-        gjp.forward(v16, geom, vg.h, out=proj16, path=args.forward_path)
+        gjp.forward(v16, geom, vg.h, out=proj16, path=args.path16 or args.forward_path)
         if ev is not None:
             ev[2].record(stream)
         gjp.adjoint(proj32, geom, vg.n, vg.h, out=back)
@@ -555,16 +567,16 @@ def run_gjp(args):
         else "synthetic (Shepp-Logan-shaped phantom, project-owned ellipsoids)",
         "config": {"workload": wname, "volume": list(vg.n), "detector": [cg.nv, cg.nu], "views": cg_full.n_views,
                    "launch": {"tile_u": geom.launch[0], "view_group": geom.launch[1]},
-                   "forward_path": args.forward_path,
+                   "forward_path": args.forward_path, **({"path16": args.path16} if args.path16 else {}),
                    "tap_source": {"forward_f32": "volume", k16: "z-paired copy, written per call"
-                                  if launches_per_step(args.forward_path, vg.n) > 3 else "volume"},
+                                  if launches_per_step(args.forward_path, args.path16, vg.n, cg.n_views) > 3 else "volume"},
                    "step": "forward f32 + forward bf16 + adjoint f32", "samples_per_kernel": samples_per_kernel,
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "one GPU" if world == 1 else
                    f"one scan split by views over {world} GPUs (rank views {scan.start}..{scan.stop - 1}), "
                    "adjoint volumes summed by one all-reduce"},
         "kernels": kernels, "roofline": roofline, "clocks": clocks,
-        "gpu_launches": launches_per_step(args.forward_path, vg.n) * args.steps,
+        "gpu_launches": launches_per_step(args.forward_path, args.path16, vg.n, cg.n_views) * args.steps,
         "e2e": e2e,
     }
     if world == 1 and args.content == "random" and not args.no_phantom and not args.first_views:
@@ -584,14 +596,16 @@ def run_gjp(args):
         dist.destroy_process_group()
 
 
-def launches_per_step(path: str, n) -> int:
+def launches_per_step(path: str, path16, n, n_views: int) -> int:
     """The library's kernel launches in one step: forward f32, forward bf16
     and the adjoint, plus the z-paired copy that a "pairs" forward writes
-    first (AUTO takes it for 16-bit storage; both only where the element
-    offsets fit 32 bits, the library's fits_int32 rule)."""
+    first (AUTO takes it for 16-bit storage and 32 or more views; both only
+    where the element offsets fit 32 bits, the library's fits_int32 rule)."""
     nx, ny, nz = (int(v) for v in n)
     fits = nx * ny * nz + 2 * (ny * nz + nz + 1) < 2147483647
-    return 3 + int(fits and path in ("auto", "pairs")) + int(fits and path == "pairs")
+    p16 = path16 or path
+    pairs16 = p16 == "pairs" or (p16 == "auto" and n_views >= 32)
+    return 3 + int(fits and pairs16) + int(fits and path == "pairs")
 
 
 def phantom_kernels(args, gjp, geom, vg, cg, dev, stream, hbm, peak_kind, k16):
@@ -605,7 +619,7 @@ def phantom_kernels(args, gjp, geom, vg, cg, dev, stream, hbm, peak_kind, k16):
     p16 = torch.empty_like(p32)
     bk = torch.empty(vg.n, device=dev)
     fns = {"forward_f32": lambda: gjp.forward(vol, geom, vg.h, out=p32, path=args.forward_path),
-           k16: lambda: gjp.forward(v16, geom, vg.h, out=p16, path=args.forward_path),
+           k16: lambda: gjp.forward(v16, geom, vg.h, out=p16, path=args.path16 or args.forward_path),
            "adjoint_f32": lambda: gjp.adjoint(p32, geom, vg.n, vg.h, out=bk)}
     counts = sample_counts(vg, cg)
     foot = np.array(gjp.footprint_voxels(geom, vg.n, vg.h, device=dev), dtype=np.float64)

@@ -165,8 +165,8 @@ gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_
 /* Kernel family used by gjp_forward_ex. */
 typedef enum {
     GJP_PATH_AUTO = 0,   /* the library's fastest family for the call (forward: PAIRS for
-                            16-bit storage where it applies, else GATHER; adjoint:
-                            COMBINE) */
+                            16-bit storage and 32 or more views where it applies, else
+                            GATHER; adjoint: COMBINE) */
     GJP_PATH_GATHER = 1, /* one thread per ray, taps gathered from global memory */
     GJP_PATH_SLAB = 2,   /* detector tiles stream per-plane voxel boxes into shared memory
                             with TMA; needs a 16-byte aligned volume whose z row is a
@@ -216,11 +216,13 @@ typedef enum {
  * gjp_trim_workspace).  PAIRS returns GJP_ERR_UNSUPPORTED while `stream`
  * is being captured into a CUDA graph and for grids whose element offsets
  * do not fit 32 bits, and GJP_ERR_OOM when the copy cannot be allocated.
- * GJP_PATH_AUTO takes PAIRS for bfloat16 and float16 storage (measured
- * faster than GATHER: half the load instructions, same L1 lines per load)
- * and falls back to GATHER wherever PAIRS returns one of those statuses;
- * for float32 it takes GATHER (the 8-byte copy doubles the footprint in the
- * caches and measured slower).
+ * GJP_PATH_AUTO takes PAIRS for bfloat16 and float16 storage when g has at
+ * least 32 views (measured faster than GATHER there: half the load
+ * instructions, same L1 lines per load; with fewer views the volume is
+ * read from DRAM about once and the copy only adds bytes) and falls back to
+ * GATHER wherever PAIRS returns one of those statuses; for float32 it takes
+ * GATHER (the 8-byte copy doubles the footprint in the caches and measured
+ * slower).
  */
 gjp_status gjp_forward_ex(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_t ny, int64_t nz,
                           const double voxel_size[3], const double volume_origin[3],
@@ -412,7 +414,9 @@ void gjp_batch_destroy(gjp_batch *b);
  * gjp_batch_forward -- all problems of the batch in one persistent kernel
  * launch on `stream` (preceded by a 4-byte reset of the queue counter on the
  * same stream; nothing is allocated or synchronised, so the call can be
- * captured into a CUDA graph).  Each projection is bitwise equal to
+ * captured into a CUDA graph).  The batch reads every volume directly (no
+ * z-paired copies: with them the batched launch measured slower on both
+ * batch mixes).  Each projection is bitwise equal to
  * gjp_forward of the same problem (same per-ray arithmetic and warp
  * layout).  Batches share nothing, but two launches of the same batch must
  * not overlap on the GPU (they share the queue counter).  Returns

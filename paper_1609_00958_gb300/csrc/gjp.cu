@@ -238,6 +238,26 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocksMax) gjp_forward_kernel
         forward_ray<T, Index, SPL, PAIRS>(vol, V, views + view, nu, nv, iu, iv, act, (int)threadIdx.y, pairs);
 }
 
+// The z-paired copy of a 16-bit volume whose z lines are whole 8-byte words
+// (nz % 4 == 0, 8-byte aligned base): a thread reads four voxels with one
+// 8-byte load plus the next line voxel and writes their four pair words with
+// one 16-byte store.
+__global__ void gjp_zpairs16x4_kernel(const unsigned short *__restrict__ vol, long long lines, int nz,
+                                      uint4 *__restrict__ out)
+{
+    const int quads = nz >> 2;
+    for (long long r = blockIdx.x; r < lines; r += gridDim.x) {
+        const unsigned short *line = vol + r * nz;
+        const uint2 *src = reinterpret_cast<const uint2 *>(line);
+        uint4 *o = out + r * quads;
+        for (int k = threadIdx.x; k < quads; k += blockDim.x) {
+            const uint2 w = __ldg(src + k);                              // voxels 4k .. 4k + 3
+            const unsigned next = 4 * k + 4 < nz ? (unsigned)__ldg(line + 4 * k + 4) : 0u;
+            o[k] = make_uint4(w.x, __funnelshift_r(w.x, w.y, 16), w.y, (w.y >> 16) | (next << 16));
+        }
+    }
+}
+
 // The z-paired copy of a volume (read by the row-table march): element e
 // holds voxels e and e + 1 of its z line, the upper one zero at the last z.
 // One block per z line at a time; consecutive threads take consecutive z.
@@ -1582,6 +1602,7 @@ cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *ta
 }
 
 // Writes the z-paired copy of vol (n[0] n[1] lines of n[2] voxels) to out.
+// 16-bit volumes whose lines are whole 8-byte words take the 4-voxel form.
 template <typename T>
 cudaError_t launch_zpairs(const T *vol, const int64_t n[3], typename PairOf<T>::type *out, cudaStream_t s)
 {
@@ -1589,8 +1610,17 @@ cudaError_t launch_zpairs(const T *vol, const int64_t n[3], typename PairOf<T>::
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int threads = n[2] >= 256 ? 256 : 128;
     const long long blocks = std::min<long long>(lines, (long long)std::max(sms, 1) * 8);
+    if constexpr (!std::is_same<T, float>::value) {
+        if (n[2] % 4 == 0 && reinterpret_cast<uintptr_t>(vol) % 8 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) {
+            const int quads = (int)(n[2] / 4);
+            const int threads = quads >= 128 ? 128 : 32 * ((quads + 31) / 32);
+            gjp_zpairs16x4_kernel<<<(unsigned)blocks, threads, 0, s>>>(
+                reinterpret_cast<const unsigned short *>(vol), lines, (int)n[2], reinterpret_cast<uint4 *>(out));
+            return cudaGetLastError();
+        }
+    }
+    const int threads = n[2] >= 256 ? 256 : 128;
     gjp_zpairs_kernel<T><<<(unsigned)blocks, threads, 0, s>>>(vol, lines, (int)n[2], out);
     return cudaGetLastError();
 }
@@ -1638,13 +1668,17 @@ gjp_status forward_typed(const void *d_volume, gjp_dtype dt, const int64_t n[3],
         if (path == GJP_PATH_SLAB) return GJP_ERR_UNSUPPORTED;
     }
     // The z-paired copy: on request (PAIRS), and taken by AUTO for 16-bit
-    // storage when the offsets fit 32 bits and the copy can be allocated
-    // (otherwise AUTO reads the volume directly).  Its results are bitwise
-    // those of GATHER.  Measured on the 512^3 / 360-view workload it makes
-    // the 16-bit forward 11% faster (copy included) and the float32 one 35%
-    // slower (8-byte words: twice the footprint in L1 and L2).
+    // storage when the scan has at least kPairsMinViews views, the offsets
+    // fit 32 bits and the copy can be allocated (otherwise AUTO reads the
+    // volume directly).  Its results are bitwise those of GATHER.  Measured
+    // on the 512^3 / 360-view workload it makes the 16-bit forward 11%
+    // faster (copy included) and the float32 one 35% slower (8-byte words:
+    // twice the footprint in L1 and L2).  With few views the volume is read
+    // from DRAM about once and the copy only adds bytes: at 128^3 .. 512^3
+    // it lost with 4 and 16 views and won with 64 and more.
     constexpr bool kPairsAuto = !std::is_same<T, float>::value;
-    if (path == GJP_PATH_PAIRS || (path == GJP_PATH_AUTO && kPairsAuto && i32)) {
+    constexpr int kPairsMinViews = 32;
+    if (path == GJP_PATH_PAIRS || (path == GJP_PATH_AUTO && kPairsAuto && i32 && g.n_views >= kPairsMinViews)) {
         if (!i32) return GJP_ERR_UNSUPPORTED;
         using P = typename PairOf<T>::type;
         void *ws = nullptr;

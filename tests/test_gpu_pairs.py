@@ -47,8 +47,8 @@ def _case(name):
         vg = VolumeGeometry.centred((3, 2, 2))
         cg = synth.circular(4, 7, 35, 12.0, 24.0, 0.3, angles=[0.1, 0.9, 2.0, 4.4])
         return rng.random(vg.n, dtype=np.float32), vg, cg
-    if name == "c2_small":
-        vg, cg = synth.scaled_c2_geometry(128, 128, 24, 10.0)
+    if name == "c2_small":                            # 32 views or more: AUTO takes the paired copy
+        vg, cg = synth.scaled_c2_geometry(128, 128, 40, 10.0)
         return synth.random_field(vg.n, seed=1), vg, cg
     raise ValueError(name)
 
@@ -140,3 +140,22 @@ def test_trim_workspace(gjp):
     gjp.trim_workspace()
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+def test_pairs_unaligned_volume(gjp):
+    """A 16-bit volume that starts 2 bytes past an 8-byte boundary takes the
+    one-voxel copy; nz = 128 would otherwise take the four-voxel one."""
+    vg, cg = synth.scaled_c2_geometry(64, 64, 6, 10.0)
+    vol = synth.random_field((64, 64, 128), seed=3)
+    vg = VolumeGeometry.centred((64, 64, 128))
+    flat = torch.empty(vol.size + 1, dtype=torch.bfloat16, device="cuda")
+    v = flat[1:].view(vol.shape)
+    v.copy_(torch.from_numpy(vol).cuda())
+    assert v.data_ptr() % 8 != 0
+    g = gjp.Geometry.from_cone(cg)
+    a = gjp.forward(v, g, vg.h, path="gather")
+    b = gjp.forward(v, g, vg.h, path="pairs")
+    gjp.stream_status()
+    assert torch.equal(a, b)
+    ref = gjp.forward(v.contiguous().clone(), g, vg.h, path="pairs")   # aligned copy: the four-voxel form
+    assert torch.equal(a, ref)
