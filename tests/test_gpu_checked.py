@@ -5,8 +5,8 @@ arithmetic; a wrong trim would read or reduce outside the grid without any
 other symptom than a parity drift.  Here the checked library runs the small
 cases of the parity tests -- random and steep geometries (z-driven rays),
 ragged detectors, anisotropic and off-centre grids, tiny grids, w_spl, a
-field-of-view cylinder, 16-bit storage, the gather / prefetch / batched
-forwards and the combined / scatter adjoints -- and must report no tap
+field-of-view cylinder, 16-bit storage, the gather / z-paired / prefetch /
+batched forwards and the combined / scatter adjoints -- and must report no tap
 outside the grid (gjp_stream_status == GJP_OK) and match the FP64 oracle.
 A self-test shows the report path works: one thread records an
 out-of-grid tap through the same check (indices only, no memory access)."""
@@ -102,16 +102,19 @@ def test_selftest_reports_a_tap_outside_the_grid(gjp):
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("path", ["auto", "prefetch"])
+@pytest.mark.parametrize("path", ["auto", "prefetch", "pairs"])
 def test_checked_forward_stays_in_the_grid(gjp, case, path):
     import oracle
     from paper_1609_00958_gb300 import _capi
     vol, vg, cg, opts = _case(case)
     if path == "prefetch" and opts:
         pytest.skip("the prefetch family implements w_lin without clipping")
+    if path == "pairs":                           # the z-paired copy serves 16-bit storage
+        vol = torch.from_numpy(vol).to(torch.bfloat16).float().numpy()
     g = _geometry(gjp, cg, opts)
+    dv = torch.from_numpy(vol).cuda()
     try:
-        out = gjp.forward(torch.from_numpy(vol).cuda(), g, vg.h, vg.origin, path=path)
+        out = gjp.forward(dv.to(torch.bfloat16) if path == "pairs" else dv, g, vg.h, vg.origin, path=path)
     except gjp.GjpError as e:
         if e.status == _capi.GJP_ERR_UNSUPPORTED:      # e.g. TMA needs a 16-byte aligned z extent
             pytest.skip(f"{path} does not take this grid")
