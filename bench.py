@@ -1010,6 +1010,7 @@ def batch_measure(specs, warmup, steps, dev, clocks=False):
         separate()
     ms["separate_launches_graph"] = timed(sep_graph.replay, steps)
     batch = gjp.Batch(items)
+    launches = batch.launches
     ms["batched"] = timed(batch.forward, steps)
     tunings = batch.autotune(reps=2)
     ms["batched_autotuned"] = timed(batch.forward, steps)
@@ -1023,16 +1024,16 @@ def batch_measure(specs, warmup, steps, dev, clocks=False):
         clk = c.summary()
     else:
         ms["batched_autotuned_graph"] = timed(graph.replay, steps)
-    return {k: round(v, 3) for k, v in ms.items()}, (samples, alg_bytes), tunings, clk
+    return {k: round(v, 3) for k, v in ms.items()}, (samples, alg_bytes, launches), tunings, clk
 
 
 def batch_summary(ms, counts):
-    samples, alg_bytes = counts
+    samples, alg_bytes, launches = counts
     gsps = lambda m: round(samples / (m * 1e-3) / 1e9, 2)
     hbm, peak_kind = peaks()
     best = ms["batched_autotuned_graph"]
     return {"ms": ms, "gsamples_s": {k: gsps(v) for k, v in ms.items()},
-            "algorithmic_gb": round(alg_bytes / 1e9, 3),
+            "algorithmic_gb": round(alg_bytes / 1e9, 3), "launches_per_batched_forward": launches,
             "frac_of_" + peak_kind + "_hbm": round(alg_bytes / (best * 1e-3) / 1e9 / hbm, 4),
             "speedup_vs_separate": round(ms["separate_launches"] / ms["batched_autotuned_graph"], 3),
             "speedup_vs_separate_graph": round(ms["separate_launches_graph"] / ms["batched_autotuned_graph"], 3),
@@ -1072,7 +1073,7 @@ def run_batch(args):
         "data": "synthetic (seeded problems: Shepp-Logan-shaped phantoms and uniform random fields)",
         "config": {"workload": name, "samples": samples, "problems": len(specs)},
         **out, "tuning": [{"tile_u": t, "view_group": v} for t, v in tunings],
-        "clocks": clocks, "gpu_launches": args.steps,
+        "clocks": clocks, "gpu_launches": counts[2] * args.steps,
     }), flush=True)
 
 

@@ -400,8 +400,12 @@ typedef struct gjp_batch gjp_batch;
  * tile of one view, 128 rays) and problems with the most planes per ray
  * are queued first.  Builds each geometry's device table on the current
  * device (as gjp_forward would) and allocates a few hundred bytes per
- * problem; the problems array is copied, but the volumes, projections and
- * geometries it points to must stay valid while the batch is used.  Each
+ * problem, plus a z-paired copy (4 bytes per voxel; see GJP_PATH_PAIRS and
+ * gjp_batch_forward) for each bfloat16 or float16 problem that runs alone
+ * over 32 or more views -- a copy that cannot be allocated leaves its
+ * problem reading the volume, with the same results.  The problems array
+ * is copied, but the volumes, projections and geometries it points to must
+ * stay valid while the batch is used.  Each
  * problem starts with its geometry's launch shape (gjp_geometry_set_launch;
  * a tile_u of 8 becomes 4).  Make this call before capturing a stream.
  */
@@ -411,12 +415,15 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
 void gjp_batch_destroy(gjp_batch *b);
 
 /*
- * gjp_batch_forward -- all problems of the batch in one persistent kernel
- * launch on `stream` (preceded by a 4-byte reset of the queue counter on the
- * same stream; nothing is allocated or synchronised, so the call can be
- * captured into a CUDA graph).  The batch reads every volume directly (no
- * z-paired copies: with them the batched launch measured slower on both
- * batch mixes).  Each projection is bitwise equal to
+ * gjp_batch_forward -- the problems of the batch on `stream`: a problem
+ * whose work items fill the GPU's resident blocks 16 times or more runs as
+ * its own launch of the gather forward (the kernels of gjp_forward; a
+ * bfloat16 or float16 one over 32 or more views first rewrites its z-paired
+ * copy, allocated by gjp_batch_create and kept with the batch), and all
+ * other problems share one persistent kernel launch (preceded by a 4-byte
+ * reset of the queue counter).  Nothing is allocated or synchronised, so
+ * the call can be captured into a CUDA graph.  Each projection is bitwise
+ * equal to
  * gjp_forward of the same problem (same per-ray arithmetic and warp
  * layout).  Batches share nothing, but two launches of the same batch must
  * not overlap on the GPU (they share the queue counter).  Returns
@@ -425,6 +432,11 @@ void gjp_batch_destroy(gjp_batch *b);
  */
 gjp_status gjp_batch_forward(const gjp_batch *b, void *stream);
 
+/* The number of kernel launches one gjp_batch_forward makes (solo
+ * problems' copy and gather launches, plus the persistent launch when the
+ * queue holds problems; the counter reset is a memset, not a kernel). */
+gjp_status gjp_batch_launch_count(const gjp_batch *b, int *launches);
+
 /*
  * gjp_batch_autotune -- for every problem, times the batched launch of that
  * problem alone on its first 24 views for each tile shape (tile_u = 1, 2 or
@@ -432,7 +444,9 @@ gjp_status gjp_batch_forward(const gjp_batch *b, void *stream);
  * views), `reps` timed runs after one warm-up each, and keeps the fastest.
  * Shapes that are fastest alone need not be fastest in the shared queue:
  * the whole batch is timed before and after, and the previous shapes are
- * restored if the tuned ones are slower.  Writes valid projections and
+ * restored if the tuned ones are slower.  A problem that runs as its own
+ * launch takes the chosen tile_u as its blocks' detector columns (32 rows
+ * each) and the chosen interleaving.  Writes valid projections and
  * synchronises `stream`; not for use during stream capture.  The choice
  * changes speed only, never a result.
  */

@@ -296,6 +296,14 @@ class Batch:
             tuning_cache.store(cache, key, gpu, tunings)
         return tunings
 
+    @property
+    def launches(self) -> int:
+        """Kernel launches per ``forward()`` (``gjp_batch_launch_count``)."""
+        st, n = _capi.gjp_batch_launch_count(self.handle)
+        if st != _capi.GJP_OK:
+            raise GjpError(st, "gjp_batch_launch_count")
+        return n
+
     def tuning(self, i: int):
         st, tu, vg = _capi.gjp_batch_get_tuning(self.handle, i)
         if st != _capi.GJP_OK:

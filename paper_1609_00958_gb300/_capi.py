@@ -44,7 +44,7 @@ EXPORTS = ("gjp_geometry_create", "gjp_geometry_destroy", "gjp_geometry_info", "
            "gjp_forward_ex", "gjp_forward_noalloc", "gjp_stream_status", "gjp_selftest_wait_timeout",
            "gjp_selftest_tap_check", "gjp_debug_fail_allocations", "gjp_trim_workspace", "gjp_adjoint", "gjp_adjoint_ex",
            "gjp_footprint", "gjp_batch_create", "gjp_batch_destroy", "gjp_batch_forward",
-           "gjp_batch_autotune", "gjp_batch_get_tuning", "gjp_batch_set_tuning", "gjp_status_string")
+           "gjp_batch_autotune", "gjp_batch_launch_count", "gjp_batch_get_tuning", "gjp_batch_set_tuning", "gjp_status_string")
 
 #: view limit of gjp_forward_noalloc (GJP_NOALLOC_MAX_VIEWS in include/gjp.h)
 GJP_NOALLOC_MAX_VIEWS = 1024
@@ -123,6 +123,8 @@ def load(path: str | None = None):
     lib.gjp_batch_forward.restype = _I
     lib.gjp_batch_autotune.argtypes = [_P, _P, _I]
     lib.gjp_batch_autotune.restype = _I
+    lib.gjp_batch_launch_count.argtypes = [_P, ctypes.POINTER(_I)]
+    lib.gjp_batch_launch_count.restype = _I
     lib.gjp_batch_get_tuning.argtypes = [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
     lib.gjp_batch_get_tuning.restype = _I
     lib.gjp_batch_set_tuning.argtypes = [_P, _I, _I, _I]
@@ -275,6 +277,12 @@ def gjp_batch_forward(handle, stream: int) -> int:
 
 def gjp_batch_autotune(handle, stream: int, reps: int) -> int:
     return load().gjp_batch_autotune(_P(handle) if handle else None, _P(stream), int(reps))
+
+
+def gjp_batch_launch_count(handle):
+    n = _I()
+    st = load().gjp_batch_launch_count(_P(handle) if handle else None, ctypes.byref(n))
+    return st, n.value
 
 
 def gjp_batch_get_tuning(handle, problem: int):

@@ -1575,18 +1575,19 @@ cudaError_t launch_gather_pf(const T *vol, gjp_dtype dt, const int64_t n[3], con
 // pairs: the z-paired copy of vol for the row-table march (32-bit offsets
 // only), or null to read the taps from vol.
 template <typename T>
-cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *table, const gjp_geometry &g,
-                          bool i32, float *proj, cudaStream_t s, const typename PairOf<T>::type *pairs = nullptr)
+cudaError_t launch_gather_shaped(const T *vol, const VolParams &V, const ViewParams *table, const GatherShape &sh,
+                                 bool i32, float *proj, cudaStream_t s,
+                                 const typename PairOf<T>::type *pairs = nullptr)
 {
-    const int n_tv = (g.nv + kTileV - 1) / kTileV;
-    const int n_tu = (g.nu + g.tile_u - 1) / g.tile_u;
-    const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)g.n_views);
-    const dim3 block(kTileV, g.tile_u);
-    const bool spl = g.weight == GJP_WEIGHT_SPL;
-    const int nvw = g.n_views, vgp = launch_view_group(g, V.n);
-    const size_t rows = (size_t)g.tile_u * 32 * sizeof(uint2);   // row tables (32-bit offsets only)
+    const int n_tv = (sh.nv + kTileV - 1) / kTileV;
+    const int n_tu = (sh.nu + sh.tile_u - 1) / sh.tile_u;
+    const dim3 grid((unsigned)(n_tv * n_tu), (unsigned)sh.n_views);
+    const dim3 block(kTileV, sh.tile_u);
+    const bool spl = sh.spl;
+    const int nu = sh.nu, nv = sh.nv, nvw = sh.n_views, vgp = sh.view_group;
+    const size_t rows = (size_t)sh.tile_u * 32 * sizeof(uint2);   // row tables (32-bit offsets only)
 #define GJP_LAUNCH_FWD(I, S, P, SMEM)                                                                              \
-    gjp_forward_kernel<T, I, S, P><<<grid, block, SMEM, s>>>(vol, V, table, g.nu, g.nv, n_tv, nvw, vgp, proj, pairs)
+    gjp_forward_kernel<T, I, S, P><<<grid, block, SMEM, s>>>(vol, V, table, nu, nv, n_tv, nvw, vgp, proj, pairs)
     if (i32 && pairs) {
         if (spl) GJP_LAUNCH_FWD(int, true, true, rows);
         else GJP_LAUNCH_FWD(int, false, true, rows);
@@ -1599,6 +1600,14 @@ cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *ta
     }
 #undef GJP_LAUNCH_FWD
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather(const T *vol, const VolParams &V, const ViewParams *table, const gjp_geometry &g,
+                          bool i32, float *proj, cudaStream_t s, const typename PairOf<T>::type *pairs = nullptr)
+{
+    const GatherShape sh{g.nu, g.nv, g.n_views, g.tile_u, launch_view_group(g, V.n), g.weight == GJP_WEIGHT_SPL};
+    return launch_gather_shaped<T>(vol, V, table, sh, i32, proj, s, pairs);
 }
 
 // Writes the z-paired copy of vol (n[0] n[1] lines of n[2] voxels) to out.
@@ -1623,6 +1632,28 @@ cudaError_t launch_zpairs(const T *vol, const int64_t n[3], typename PairOf<T>::
     const int threads = n[2] >= 256 ? 256 : 128;
     gjp_zpairs_kernel<T><<<(unsigned)blocks, threads, 0, s>>>(vol, lines, (int)n[2], out);
     return cudaGetLastError();
+}
+
+cudaError_t forward_gather_shaped(const void *vol, gjp_dtype dt, const VolParams &V, const ViewParams *table,
+                                  const GatherShape &sh, bool i32, float *proj, const void *pairs, cudaStream_t s)
+{
+    switch (dt) {
+    case GJP_F32:
+        return launch_gather_shaped<float>(static_cast<const float *>(vol), V, table, sh, i32, proj, s);
+    case GJP_BF16:
+        return launch_gather_shaped<__nv_bfloat16>(static_cast<const __nv_bfloat16 *>(vol), V, table, sh, i32, proj, s,
+                                                   static_cast<const unsigned *>(pairs));
+    default:
+        return launch_gather_shaped<__half>(static_cast<const __half *>(vol), V, table, sh, i32, proj, s,
+                                            static_cast<const unsigned *>(pairs));
+    }
+}
+
+cudaError_t write_zpairs16(const void *vol, gjp_dtype dt, const int64_t n[3], void *out, cudaStream_t s)
+{
+    if (dt == GJP_BF16)
+        return launch_zpairs<__nv_bfloat16>(static_cast<const __nv_bfloat16 *>(vol), n, static_cast<unsigned *>(out), s);
+    return launch_zpairs<__half>(static_cast<const __half *>(vol), n, static_cast<unsigned *>(out), s);
 }
 
 template <typename T>

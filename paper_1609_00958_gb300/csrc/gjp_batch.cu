@@ -30,6 +30,10 @@ constexpr int kBatchThreads = kBatchWarps * 32;
 constexpr size_t kBatchRowBytes = kBatchWarps * 32 * sizeof(uint2);   // dynamic shared: row tables
 constexpr int kBatchMaxProblems = 256;
 constexpr int kTuneViews = 24;                       // views timed per autotuner candidate
+// A problem with at least this many waves of the persistent grid's blocks
+// fills the GPU alone: it runs as its own gather launch (the kernels of
+// gjp_forward), not through the shared queue.
+constexpr int kSoloWaves = 16;
 
 struct __align__(8) BatchProblem {
     const void *vol;
@@ -182,6 +186,9 @@ struct gjp_batch {
     unsigned long long *d_counter = nullptr;
     BatchProblem *d_tune = nullptr;      // one-problem queue for the autotuner
     long long *d_tune_begins = nullptr;
+    std::vector<char> solo;              // per problem (queue order): its own launch
+    std::vector<void *> solo_pairs;      // per problem: the z-paired copy of a solo 16-bit problem, or null
+    int n_queue = 0;                     // problems in the persistent queue
 };
 
 namespace {
@@ -196,12 +203,47 @@ gjp_status upload(const BatchProblem *probs, int n, BatchProblem *d_probs, long 
     return GJP_OK;
 }
 
+// Uploads the problems that share the persistent queue (the others run alone).
+gjp_status upload_queue(gjp_batch *b)
+{
+    std::vector<BatchProblem> q;
+    try {
+        for (size_t p = 0; p < b->probs.size(); ++p)
+            if (!b->solo[p]) q.push_back(b->probs[p]);
+    } catch (const std::bad_alloc &) {
+        return GJP_ERR_OOM;
+    }
+    b->n_queue = (int)q.size();
+    return q.empty() ? GJP_OK : upload(q.data(), (int)q.size(), b->d_probs, b->d_begins);
+}
+
 gjp_status launch(const gjp_batch *b, const BatchProblem *d_probs, const long long *d_begins, int n,
                   cudaStream_t s)
 {
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return GJP_ERR_CUDA;
     b->kernel<<<b->grid, kBatchThreads, kBatchRowBytes, s>>>(d_probs, d_begins, n, b->d_counter);
     return cudaGetLastError() == cudaSuccess ? GJP_OK : GJP_ERR_CUDA;
+}
+
+// One forward of the whole batch: each solo problem as its own gather
+// launch (after writing its z-paired copy, if it has one), then one
+// persistent launch over the queue.
+gjp_status run_batch(const gjp_batch *b, cudaStream_t s)
+{
+    for (size_t q = 0; q < b->probs.size(); ++q) {
+        if (!b->solo[q]) continue;
+        const BatchProblem &P = b->probs[q];
+        const gjp_dtype dt = (gjp_dtype)(P.kind & 3);
+        void *pairs = b->solo_pairs[q];
+        if (pairs) {
+            const int64_t n[3] = {P.V.n[0], P.V.n[1], P.V.n[2]};
+            if (write_zpairs16(P.vol, dt, n, pairs, s) != cudaSuccess) return GJP_ERR_CUDA;
+        }
+        const GatherShape sh{P.nu, P.nv, P.n_views, P.tile_u, P.view_group, (P.kind & 8) != 0};
+        if (forward_gather_shaped(P.vol, dt, P.V, P.table, sh, (P.kind & 4) != 0, P.proj, pairs, s) != cudaSuccess)
+            return GJP_ERR_CUDA;
+    }
+    return b->n_queue > 0 ? launch(b, b->d_probs, b->d_begins, b->n_queue, s) : GJP_OK;
 }
 
 void free_batch(gjp_batch *b)
@@ -216,6 +258,7 @@ void free_batch(gjp_batch *b)
         cudaFree(b->d_counter);
         cudaFree(b->d_tune);
         cudaFree(b->d_tune_begins);
+        for (void *q : b->solo_pairs) cudaFree(q);
         if (have) cudaSetDevice(cur);
     }
     delete b;
@@ -313,7 +356,28 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
         return GJP_ERR_CUDA;
     }
     b->grid = per_sm * sms;
-    const gjp_status st = upload(b->probs.data(), count, b->d_probs, b->d_begins);
+    // problems that fill the GPU alone run as their own launch; a 16-bit
+    // one over 32 or more views reads a z-paired copy kept with the batch
+    // (as gjp_forward's AUTO would), unless it cannot be allocated
+    try {
+        b->solo.assign(count, 0);
+        b->solo_pairs.assign(count, nullptr);
+    } catch (const std::bad_alloc &) {
+        free_batch(b);
+        return GJP_ERR_OOM;
+    }
+    for (int q = 0; q < count; ++q) {
+        const BatchProblem &P = b->probs[q];
+        if (P.items < (long long)kSoloWaves * b->grid) continue;
+        b->solo[q] = 1;
+        if ((P.kind & 3) == GJP_F32 || !(P.kind & 4) || P.n_views < 32) continue;
+        const size_t bytes = (size_t)P.V.n[0] * P.V.n[1] * P.V.n[2] * sizeof(unsigned);
+        if (!alloc_gate() || cudaMalloc(&b->solo_pairs[q], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            b->solo_pairs[q] = nullptr;
+        }
+    }
+    const gjp_status st = upload_queue(b);
     if (st != GJP_OK) {
         free_batch(b);
         return st;
@@ -331,7 +395,17 @@ gjp_status gjp_batch_forward(const gjp_batch *b, void *stream)
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GJP_ERR_CUDA;
     if (dev != b->device) return GJP_ERR_INVALID_ARG;
-    return launch(b, b->d_probs, b->d_begins, (int)b->probs.size(), (cudaStream_t)stream);
+    return run_batch(b, (cudaStream_t)stream);
+}
+
+gjp_status gjp_batch_launch_count(const gjp_batch *b, int *launches)
+{
+    if (!b || !launches) return GJP_ERR_INVALID_ARG;
+    int n = b->n_queue > 0 ? 1 : 0;
+    for (size_t q = 0; q < b->probs.size(); ++q)
+        if (b->solo[q]) n += b->solo_pairs[q] ? 2 : 1;
+    *launches = n;
+    return GJP_OK;
 }
 
 gjp_status gjp_batch_get_tuning(const gjp_batch *b, int problem, int *tile_u, int *view_group)
@@ -356,7 +430,7 @@ gjp_status gjp_batch_set_tuning(gjp_batch *b, int problem, int tile_u, int view_
     if (dev != b->device) return GJP_ERR_INVALID_ARG;
     for (size_t q = 0; q < b->order.size(); ++q)
         if (b->order[q] == problem) shape_problem(b->probs[q], tile_u, view_group, b->full_views[q]);
-    return upload(b->probs.data(), (int)b->probs.size(), b->d_probs, b->d_begins);
+    return upload_queue(b);
 }
 
 gjp_status gjp_batch_autotune(gjp_batch *b, void *stream, int reps)
@@ -378,12 +452,11 @@ gjp_status gjp_batch_autotune(gjp_batch *b, void *stream, int reps)
     // the whole batch, timed as it is now: per-problem shapes that are
     // fastest alone need not be fastest in the shared queue, so the tuned
     // shapes are kept only if the whole batch gets faster
-    const int n = (int)b->probs.size();
     auto batch_ms = [&](float &out) {
         float ms_min = 3.0e38f;
         for (int r = 0; r <= reps && st == GJP_OK; ++r) {           // r = 0 warms up
             if (cudaEventRecord(e0, s) != cudaSuccess) st = GJP_ERR_CUDA;
-            if (st == GJP_OK) st = launch(b, b->d_probs, b->d_begins, n, s);
+            if (st == GJP_OK) st = run_batch(b, s);
             if (st == GJP_OK && cudaEventRecord(e1, s) != cudaSuccess) st = GJP_ERR_CUDA;
             float ms = 0.0f;
             if (st == GJP_OK &&
@@ -425,12 +498,12 @@ gjp_status gjp_batch_autotune(gjp_batch *b, void *stream, int reps)
             }
         shape_problem(b->probs[q], best_t, best_g, b->full_views[q]);
     }
-    if (st == GJP_OK) st = upload(b->probs.data(), n, b->d_probs, b->d_begins);
+    if (st == GJP_OK) st = upload_queue(b);
     float ms_after = 0.0f;
     if (st == GJP_OK) batch_ms(ms_after);
     if (st == GJP_OK && ms_after > ms_before) {                 // keep the shapes it had
         b->probs = before;
-        st = upload(b->probs.data(), n, b->d_probs, b->d_begins);
+        st = upload_queue(b);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -141,6 +141,20 @@ bool fits_int32(const int64_t n[3]);
 // Once per function and device; a failure leaves the default in place.
 void fit_carveout(const void *func, int threads, size_t dyn_smem);
 size_t elem_size(gjp_dtype t);
+// Launch shape of one gather forward launch (grid over the detector tiles
+// of n_views views, view_group views interleaved per tile).
+struct GatherShape {
+    int nu, nv, n_views, tile_u, view_group;
+    bool spl;
+};
+// The gather forward of one problem with an explicit launch shape (used by
+// the batch for problems that fill the GPU alone): the row-table march reads
+// its taps from `pairs` -- the problem's z-paired copy, already written by
+// write_zpairs16; 16-bit storage, 32-bit offsets -- or from vol when null.
+cudaError_t forward_gather_shaped(const void *vol, gjp_dtype dt, const VolParams &V, const ViewParams *table,
+                                  const GatherShape &sh, bool i32, float *proj, const void *pairs, cudaStream_t s);
+// Writes the z-paired copy (4 bytes per voxel) of a bfloat16 or float16 volume.
+cudaError_t write_zpairs16(const void *vol, gjp_dtype dt, const int64_t n[3], void *out, cudaStream_t s);
 // Texture families (gjp_texture.cu): forward through the texture unit, and
 // release of an entry's texture arrays (with the entry's device current).
 gjp_status forward_texture(const void *d_volume, gjp_dtype dt, const int64_t n[3], const VolParams &V,
