@@ -73,6 +73,39 @@ def test_c1_matches_analytic_phantom(gjp):
     assert np.abs(gpu - ana).sum() / np.abs(ana).sum() < 0.02
 
 
+def test_linear_and_spline_weights_against_analytic_projections(gjp):
+    """Projection quality of w_lin (Eq. 13) and w_spl (Eq. 14) on the GPU:
+    l1 error of the rasterised phantom's projections against the closed-form
+    ellipsoid integrals, for 64^3, 128^3 and 256^3 grids over the same
+    64-unit cube (8 views, detectors as wide as the grid).  The paper finds
+    GJP_lin the closer of the two; both errors must also shrink with the
+    grid.  With GJP_REPORT_DIR set, the table is written there as JSON."""
+    import json
+    import os
+    table = {}
+    for n in (64, 128, 256):
+        vg = VolumeGeometry.centred((n, n, n), h=(64.0 / n,) * 3)
+        w = 64.0
+        cg = synth.circular(8, n, n, 4 * w, 8 * w, synth.covering_pitch(w, 4 * w, 8 * w, n))
+        ell = synth.ellipsoids_world(vg)
+        vol = torch.from_numpy(synth.voxelize(vg, ell, supersample=2)).cuda()
+        pa = oracle.ellipsoid_project(ell, cg, sub=8)
+        row = {}
+        for wname in ("lin", "spl"):
+            g = gjp.Geometry.from_cone(cg, weight=wname)
+            got = gjp.forward(vol, g, vg.h).double().cpu().numpy()
+            gjp.stream_status()
+            row[wname] = float(np.abs(got - pa).sum() / np.abs(pa).sum())
+        table[n] = row
+        assert row["lin"] < row["spl"], (n, row)
+    for a, b in ((64, 128), (128, 256)):
+        assert table[b]["lin"] < table[a]["lin"] and table[b]["spl"] < table[a]["spl"], table
+    out_dir = os.environ.get("GJP_REPORT_DIR")
+    if out_dir:
+        with open(os.path.join(out_dir, "weights_l1.json"), "w") as f:
+            json.dump(table, f, indent=1)
+
+
 # --- arbitrary geometry: z-driven rays, anisotropic voxels, ragged tiles ----
 
 @pytest.mark.parametrize("steep", [False, True])
