@@ -9,8 +9,9 @@ view to view so that the views together take every residue of the
 stride in u and in v): max error relative to the largest reference value (bound 1e-5 for
 float32 storage, 5e-3 for 16-bit storage) and RMS error.  Rays whose two
 largest direction components are within 1e-5 may take either driving axis
-(reading C2).  The 2048^3 phantom is voxelised without supersampling (host
-time).  With GJP_REPORT_DIR set, the error table is written there as JSON.
+(reading C2).  Both phantoms are voxelised with 2x2x2 supersampling on
+the host (about 5 s at 2048^3 on 16 cores).  With GJP_REPORT_DIR set, the
+error table is written there as JSON.
 """
 import json
 import os
@@ -66,7 +67,7 @@ def test_precision_form(gjp, n):
     vg, cg_all = synth.c3_geometry(n)
     views = np.unique(np.linspace(0, cg_all.n_views - 1, min(128, cg_all.n_views)).round().astype(int))
     cg = cg_all.subset(views)
-    vol = synth.voxelize(vg, supersample=2 if n <= 1024 else 1)
+    vol = synth.voxelize(vg, supersample=2)
     g = gjp.Geometry.from_cone(cg)
     rays = strided_rays(cg, 64)
     ref = oracle.rays(vol, vg, cg, *rays)
