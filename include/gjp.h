@@ -345,7 +345,9 @@ gjp_status gjp_footprint(const gjp_geometry *g, int view, int64_t nx, int64_t ny
  * plug-in that must not touch its host application's allocator.
  *
  * It computes exactly what gjp_forward computes (the same per-view table
- * and the same gather kernels, so the projections are bitwise equal), but
+ * and the same gather kernels, so the projections are bitwise equal; it
+ * always reads the volume itself, never a z-paired copy, whose taps are
+ * the same values), but
  * keeps the per-view table in a fixed array of GJP_NOALLOC_MAX_VIEWS entries
  * (144 bytes each, about 144 KiB) that the CUDA runtime places on every GPU
  * that loads this library and keeps there until the process exits.  The
