@@ -138,7 +138,21 @@ def test_batch_create_rejects_bad_arguments_without_a_gpu(lib):
     assert _capi.gjp_batch_forward(None, 0) == _capi.GJP_ERR_INVALID_ARG
     assert _capi.gjp_batch_autotune(None, 0, 1) == _capi.GJP_ERR_INVALID_ARG
     assert _capi.gjp_batch_get_tuning(None, 0)[0] == _capi.GJP_ERR_INVALID_ARG
+    assert _capi.gjp_batch_launch_count(None)[0] == _capi.GJP_ERR_INVALID_ARG
     _capi.gjp_batch_destroy(None)
+
+
+def test_forward_path_validation_without_cuda(lib):
+    """GJP_PATH_PAIRS is a forward family only; unknown families are
+    rejected before any CUDA call; trimming the (empty) workspace pools is
+    host-only."""
+    g = Geometry.from_cone(_geom())
+    assert _capi.gjp_forward_ex(16, 0, 8, 8, 8, (1, 1, 1), None, g.handle, 16, 99, 0) == _capi.GJP_ERR_INVALID_ARG
+    assert _capi.gjp_adjoint_ex(16, g.handle, 8, 8, 8, (1, 1, 1), None, 16, 0, _capi.GJP_PATH_PAIRS, 0) == \
+        _capi.GJP_ERR_INVALID_ARG
+    assert _capi.gjp_forward_ex(0, 0, 8, 8, 8, (1, 1, 1), None, g.handle, 16, _capi.GJP_PATH_PAIRS, 0) == \
+        _capi.GJP_ERR_INVALID_ARG
+    assert _capi.gjp_trim_workspace() == _capi.GJP_OK
 
 
 def test_debug_fail_allocations_arguments(lib):
