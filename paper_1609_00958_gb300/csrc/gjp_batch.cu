@@ -11,7 +11,10 @@
 // bitwise equal to the projections made one problem at a time.  Problems
 // are queued largest rays first (longest items first, the usual way to keep
 // the end of a dynamically scheduled queue short), and a launch is one
-// counter reset plus one kernel: both are stream operations, so a stream
+// counter reset plus one kernel.  A problem large enough to fill the GPU
+// many times over gains nothing from the shared queue: it runs as its own
+// launch of the gather forward (with a z-paired copy of a 16-bit volume
+// that the batch keeps).  All of these are stream operations, so a stream
 // that calls gjp_batch_forward can be captured into a CUDA graph.
 //
 // The tile shape and the view interleaving of each problem are launch
