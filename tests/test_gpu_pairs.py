@@ -13,6 +13,7 @@ import pytest
 import oracle
 import synth
 from synth.geometry import VolumeGeometry
+from tests import parity
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,13 +48,23 @@ def _case(name):
         vg = VolumeGeometry.centred((3, 2, 2))
         cg = synth.circular(4, 7, 35, 12.0, 24.0, 0.3, angles=[0.1, 0.9, 2.0, 4.4])
         return rng.random(vg.n, dtype=np.float32), vg, cg
+    if name == "aniso_circular":                      # anisotropic voxels, circular orbit (shared rows)
+        vg = VolumeGeometry.centred((40, 36, 32), h=(1.0, 0.9, 1.1))
+        return rng.random(vg.n, dtype=np.float32), vg, synth.cone_angle_geometry(40, 36, 6, 10.0)
+    if name == "rows_along_minus_z":                  # a warp's z indices fall lane by lane
+        vg = VolumeGeometry.centred((40, 36, 64))
+        cg = synth.cone_angle_geometry(40, 70, 5, 12.0)
+        cg.det_origin = cg.det_origin + (cg.nv - 1) * cg.det_v
+        cg.det_v = -cg.det_v
+        return rng.random(vg.n, dtype=np.float32), vg, cg
     if name == "c2_small":                            # 32 views or more: AUTO takes the paired copy
         vg, cg = synth.scaled_c2_geometry(128, 128, 40, 10.0)
         return synth.random_field(vg.n, seed=1), vg, cg
     raise ValueError(name)
 
 
-CASES = ["c1_phantom", "random_flat", "random_steep", "off_centre_ragged", "tiny_2", "c2_small"]
+CASES = ["c1_phantom", "random_flat", "random_steep", "off_centre_ragged", "tiny_2", "aniso_circular",
+         "rows_along_minus_z", "c2_small"]
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -69,6 +80,13 @@ def test_pairs_bitwise_equal_to_gather(gjp, case, weight):
         gjp.stream_status()
         assert torch.equal(a, b), (case, weight, dt)
         assert torch.equal(a, c), (case, weight, dt)
+    # the paired march against the oracle on the stored bfloat16 values
+    v16 = torch.from_numpy(vol).cuda().to(torch.bfloat16)
+    got = gjp.forward(v16, g, vg.h, vg.origin, path="pairs").cpu().numpy().astype(np.float64)
+    stored = v16.float().cpu().numpy()
+    ref = oracle.forward(stored, vg, cg, wfun=1 if weight == "spl" else 0)
+    v, iu, iv = parity.all_rays(cg)
+    parity.check_rays(got[v, iv, iu], stored, vg, cg, v, iu, iv, np.abs(ref).max(), 1e-5, ref=ref[v, iv, iu])
 
 
 def test_pairs_with_field_of_view_and_oracle(gjp):
