@@ -177,3 +177,24 @@ def test_pairs_unaligned_volume(gjp):
     assert torch.equal(a, b)
     ref = gjp.forward(v.contiguous().clone(), g, vg.h, path="pairs")   # aligned copy: the four-voxel form
     assert torch.equal(a, ref)
+
+
+def test_pairs_on_two_streams_at_once(gjp):
+    """The copy's workspace is stream-ordered: forwards of different volumes
+    on two streams, queued alternately without waiting, each read their own
+    copy and equal the volume read."""
+    vol, vg, cg = _case("c2_small")
+    g = gjp.Geometry.from_cone(cg)
+    vols = [torch.from_numpy(synth.random_field(vg.n, seed=40 + k)).cuda().to(torch.bfloat16) for k in range(4)]
+    refs = [gjp.forward(v, g, vg.h, path="gather") for v in vols]
+    outs = [torch.empty_like(r) for r in refs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        for k, v in enumerate(vols):
+            with torch.cuda.stream(streams[k % 2]):
+                gjp.forward(v, g, vg.h, out=outs[k], path="pairs")
+        torch.cuda.synchronize()
+        for k in range(len(vols)):
+            assert torch.equal(outs[k], refs[k]), (rep, k)
+            outs[k].zero_()
