@@ -581,6 +581,8 @@ def run_gjp(args):
     }
     if world == 1 and args.content == "random" and not args.no_phantom and not args.first_views:
         result["kernels_phantom"] = phantom_kernels(args, gjp, geom, vg, cg, dev, stream, hbm, peak_kind, k16)
+    if world == 1 and not args.first_views:
+        result["c1"] = c1_kernels(gjp, dev)
     if world == 1 and not args.no_batch and not args.first_views:
         name, make = BATCH_MIXES["small"]
         ms, counts, _, _ = batch_measure(make(), args.warmup, max(1, min(args.steps, 10)), dev)
@@ -596,15 +598,51 @@ def run_gjp(args):
         dist.destroy_process_group()
 
 
+def c1_kernels(gjp, dev, reps: int = 200):
+    """The three kernels of the step on the c1 case (64^3 Shepp-Logan-shaped
+    phantom, 2x2x2 supersampled, 64^2 detector, 32 views): samples/s only --
+    the volume is cache-resident, so no roofline fraction applies.  CUDA
+    events over ``reps`` back-to-back repetitions after a warm-up."""
+    import torch
+    vg, cg = synth.c1_geometry()
+    g = gjp.Geometry.from_cone(cg)
+    v32 = torch.from_numpy(synth.voxelize(vg, supersample=2)).to(dev)
+    v16 = v32.to(torch.bfloat16)
+    p32 = gjp.forward(v32, g, vg.h)
+    p16 = torch.empty_like(p32)
+    back = torch.empty(vg.n, device=dev)
+    samples = int(sample_counts(vg, cg).sum())
+    fns = {"forward_f32": lambda: gjp.forward(v32, g, vg.h, out=p32),
+           "forward_bf16": lambda: gjp.forward(v16, g, vg.h, out=p16),
+           "adjoint_f32": lambda: gjp.adjoint(p32, g, vg.n, vg.h, out=back)}
+    out = {"workload": "c1: 64^3 phantom, 64^2 detector, 32 views (cache-resident; samples/s only)",
+           "samples_per_kernel": samples}
+    for k, f in fns.items():
+        for _ in range(10):
+            f()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            f()
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / reps
+        out[k] = {"ms": round(ms, 5), "gsamples_s": round(samples / (ms * 1e-3) / 1e9, 2)}
+    return out
+
+
 def launches_per_step(path: str, path16, n, n_views: int) -> int:
     """The library's kernel launches in one step: forward f32, forward bf16
     and the adjoint, plus the z-paired copy that a "pairs" forward writes
-    first (AUTO takes it for 16-bit storage and 32 or more views; both only
-    where the element offsets fit 32 bits, the library's fits_int32 rule)."""
+    first (AUTO takes it for 16-bit storage over 32 or more views and 2^27
+    view-voxels; both only where the element offsets fit 32 bits, the
+    library's fits_int32 rule)."""
     nx, ny, nz = (int(v) for v in n)
     fits = nx * ny * nz + 2 * (ny * nz + nz + 1) < 2147483647
     p16 = path16 or path
-    pairs16 = p16 == "pairs" or (p16 == "auto" and n_views >= 32)
+    pays = n_views >= 32 and n_views * nx * ny * nz >= 2 ** 27      # the library's pairs_pay rule
+    pairs16 = p16 == "pairs" or (p16 == "auto" and pays)
     return 3 + int(fits and pairs16) + int(fits and path == "pairs")
 
 
@@ -897,7 +935,7 @@ def cpu_baseline(args, gjp, vg, cg, proj32, proj16):
                       "values and one adjoint; the adjoint includes summing its per-thread private volumes once "
                       "per block",
             "seconds": round(leg["seconds"], 3), "kernels": leg["kernels"],
-            "error_vs_oracle": leg["error_vs_oracle"]}
+            "c1": leg.get("c1"), "error_vs_oracle": leg["error_vs_oracle"]}
 
 
 def run_oracle_leg(args):
@@ -912,7 +950,23 @@ def run_oracle_leg(args):
             np.load(os.path.join(args.oracle_leg, f"p16_{bi}.npy")),
             np.load(os.path.join(args.oracle_leg, f"back_{bi}.npy"))) for bi in range(len(spec["blocks"]))]
     out = oracle_leg(vg, cg, vol_np, counts, spec["blocks"], spec["warm"], gpu=gpu)
+    out["c1"] = oracle_c1()
     print(json.dumps(out), flush=True)
+
+
+def oracle_c1():
+    """The oracle on the whole c1 case (64^3 phantom, 32 views), the three
+    calls of a step after one warm-up call."""
+    import oracle
+    vg, cg = synth.c1_geometry()
+    vol = synth.voxelize(vg, supersample=2)
+    threads = oracle_threads()
+    counts = sample_counts(vg, cg)
+    oracle_warmup(oracle, vg, cg, vol, threads)
+    times, smp, _ = oracle_block(oracle, vg, cg, vol, bf16_widened(vol), list(range(cg.n_views)), threads, counts)
+    value, total_t, per_kernel = oracle_rates([times], [smp])
+    return {"value": value, "unit": UNIT, "seconds": total_t, "kernels": per_kernel, "threads": threads,
+            "sample": "the whole c1 case: 32 views, forward f32, forward bf16-stored values, adjoint"}
 
 
 def run_reference(args):

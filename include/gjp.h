@@ -165,8 +165,8 @@ gjp_status gjp_forward(const void *d_volume, gjp_dtype dtype, int64_t nx, int64_
 /* Kernel family used by gjp_forward_ex. */
 typedef enum {
     GJP_PATH_AUTO = 0,   /* the library's fastest family for the call (forward: PAIRS for
-                            16-bit storage and 32 or more views where it applies, else
-                            GATHER; adjoint: COMBINE) */
+                            16-bit storage over 32 or more views and 2^27 view-voxels
+                            where it applies, else GATHER; adjoint: COMBINE) */
     GJP_PATH_GATHER = 1, /* one thread per ray, taps gathered from global memory */
     GJP_PATH_SLAB = 2,   /* detector tiles stream per-plane voxel boxes into shared memory
                             with TMA; needs a 16-byte aligned volume whose z row is a
@@ -217,9 +217,10 @@ typedef enum {
  * is being captured into a CUDA graph and for grids whose element offsets
  * do not fit 32 bits, and GJP_ERR_OOM when the copy cannot be allocated.
  * GJP_PATH_AUTO takes PAIRS for bfloat16 and float16 storage when g has at
- * least 32 views (measured faster than GATHER there: half the load
- * instructions, same L1 lines per load; with fewer views the volume is
- * read from DRAM about once and the copy only adds bytes) and falls back to
+ * least 32 views and views x voxels is at least 2^27 (measured faster than
+ * GATHER there: half the load instructions, same L1 lines per load; with
+ * fewer views the volume is read from DRAM about once and the copy only
+ * adds bytes, and below that work the copy is not repaid) and falls back to
  * GATHER wherever PAIRS returns one of those statuses; for float32 it takes
  * GATHER (the 8-byte copy doubles the footprint in the caches and measured
  * slower).
@@ -404,7 +405,7 @@ typedef struct gjp_batch gjp_batch;
  * device (as gjp_forward would) and allocates a few hundred bytes per
  * problem, plus a z-paired copy (4 bytes per voxel; see GJP_PATH_PAIRS and
  * gjp_batch_forward) for each bfloat16 or float16 problem that runs alone
- * over 32 or more views -- a copy that cannot be allocated leaves its
+ * where AUTO would take the copy -- a copy that cannot be allocated leaves its
  * problem reading the volume, with the same results.  The problems array
  * is copied, but the volumes, projections and geometries it points to must
  * stay valid while the batch is used.  Each
@@ -420,8 +421,8 @@ void gjp_batch_destroy(gjp_batch *b);
  * gjp_batch_forward -- the problems of the batch on `stream`: a problem
  * whose work items fill the GPU's resident blocks 16 times or more runs as
  * its own launch of the gather forward (the kernels of gjp_forward; a
- * bfloat16 or float16 one over 32 or more views first rewrites its z-paired
- * copy, allocated by gjp_batch_create and kept with the batch), and all
+ * bfloat16 or float16 one where AUTO would take the copy first rewrites its
+ * z-paired copy, allocated by gjp_batch_create and kept with the batch), and all
  * other problems share one persistent kernel launch (preceded by a 4-byte
  * reset of the queue counter).  Nothing is allocated or synchronised, so
  * the call can be captured into a CUDA graph.  Each projection is bitwise

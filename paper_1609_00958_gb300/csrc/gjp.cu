@@ -78,6 +78,18 @@ cudaMemPool_t pairs_pool(int dev)
     return pool;
 }
 
+// Whether AUTO's 16-bit forward reads a z-paired copy: 32 or more views
+// and at least 2^27 view-voxels.  With few views the volume is read from
+// DRAM about once and the copy only adds bytes (at 128^3 .. 512^3 it lost
+// with 4 and 16 views and won with 64 and more); with little work the copy
+// kernel and its allocation are not repaid (64^3 with 32 views: 30.6 vs
+// 24.7 us, 128^3 with 32 views: 91.3 vs 90.2 us; 128^3 with 64 views and
+// 192^3 with 32 won).
+bool pairs_pay(int n_views, const int64_t n[3])
+{
+    return n_views >= 32 && (double)n_views * (double)n[0] * (double)n[1] * (double)n[2] >= 134217728.0;
+}
+
 // Allocates `bytes` on stream s for the z-paired copy.  GJP_ERR_UNSUPPORTED
 // while s is being captured into a graph (the copy would become a graph
 // allocation); GJP_ERR_OOM when the allocation gate refuses or the device
@@ -1699,17 +1711,13 @@ gjp_status forward_typed(const void *d_volume, gjp_dtype dt, const int64_t n[3],
         if (path == GJP_PATH_SLAB) return GJP_ERR_UNSUPPORTED;
     }
     // The z-paired copy: on request (PAIRS), and taken by AUTO for 16-bit
-    // storage when the scan has at least kPairsMinViews views, the offsets
-    // fit 32 bits and the copy can be allocated (otherwise AUTO reads the
-    // volume directly).  Its results are bitwise those of GATHER.  Measured
-    // on the 512^3 / 360-view workload it makes the 16-bit forward 11%
-    // faster (copy included) and the float32 one 35% slower (8-byte words:
-    // twice the footprint in L1 and L2).  With few views the volume is read
-    // from DRAM about once and the copy only adds bytes: at 128^3 .. 512^3
-    // it lost with 4 and 16 views and won with 64 and more.
+    // storage when pairs_pay(), the offsets fit 32 bits and the copy can be
+    // allocated (otherwise AUTO reads the volume directly).  Its results are
+    // bitwise those of GATHER.  Measured on the 512^3 / 360-view workload it
+    // makes the 16-bit forward 11% faster (copy included) and the float32
+    // one 35% slower (8-byte words: twice the footprint in L1 and L2).
     constexpr bool kPairsAuto = !std::is_same<T, float>::value;
-    constexpr int kPairsMinViews = 32;
-    if (path == GJP_PATH_PAIRS || (path == GJP_PATH_AUTO && kPairsAuto && i32 && g.n_views >= kPairsMinViews)) {
+    if (path == GJP_PATH_PAIRS || (path == GJP_PATH_AUTO && kPairsAuto && i32 && pairs_pay(g.n_views, n))) {
         if (!i32) return GJP_ERR_UNSUPPORTED;
         using P = typename PairOf<T>::type;
         void *ws = nullptr;

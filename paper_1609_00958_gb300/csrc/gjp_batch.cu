@@ -360,8 +360,8 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
     }
     b->grid = per_sm * sms;
     // problems that fill the GPU alone run as their own launch; a 16-bit
-    // one over 32 or more views reads a z-paired copy kept with the batch
-    // (as gjp_forward's AUTO would), unless it cannot be allocated
+    // one reads a z-paired copy kept with the batch where gjp_forward's AUTO
+    // would (pairs_pay), unless it cannot be allocated
     try {
         b->solo.assign(count, 0);
         b->solo_pairs.assign(count, nullptr);
@@ -373,7 +373,8 @@ gjp_status gjp_batch_create(const gjp_problem *problems, int count, gjp_batch **
         const BatchProblem &P = b->probs[q];
         if (P.items < (long long)kSoloWaves * b->grid) continue;
         b->solo[q] = 1;
-        if ((P.kind & 3) == GJP_F32 || !(P.kind & 4) || P.n_views < 32) continue;
+        const int64_t dims[3] = {P.V.n[0], P.V.n[1], P.V.n[2]};
+        if ((P.kind & 3) == GJP_F32 || !(P.kind & 4) || !pairs_pay(P.n_views, dims)) continue;
         const size_t bytes = (size_t)P.V.n[0] * P.V.n[1] * P.V.n[2] * sizeof(unsigned);
         if (!alloc_gate() || cudaMalloc(&b->solo_pairs[q], bytes) != cudaSuccess) {
             cudaGetLastError();

@@ -153,6 +153,9 @@ struct GatherShape {
 // write_zpairs16; 16-bit storage, 32-bit offsets -- or from vol when null.
 cudaError_t forward_gather_shaped(const void *vol, gjp_dtype dt, const VolParams &V, const ViewParams *table,
                                   const GatherShape &sh, bool i32, float *proj, const void *pairs, cudaStream_t s);
+// Whether a 16-bit forward over n_views views of grid n is worth a z-paired
+// copy (the rule AUTO follows; gjp.cu).
+bool pairs_pay(int n_views, const int64_t n[3]);
 // Writes the z-paired copy (4 bytes per voxel) of a bfloat16 or float16 volume.
 cudaError_t write_zpairs16(const void *vol, gjp_dtype dt, const int64_t n[3], void *out, cudaStream_t s);
 // Texture families (gjp_texture.cu): forward through the texture unit, and

@@ -57,8 +57,8 @@ def _case(name):
         cg.det_origin = cg.det_origin + (cg.nv - 1) * cg.det_v
         cg.det_v = -cg.det_v
         return rng.random(vg.n, dtype=np.float32), vg, cg
-    if name == "c2_small":                            # 32 views or more: AUTO takes the paired copy
-        vg, cg = synth.scaled_c2_geometry(128, 128, 40, 10.0)
+    if name == "c2_small":                            # 64 views of 128^3 = 2^27: AUTO takes the paired copy
+        vg, cg = synth.scaled_c2_geometry(128, 128, 64, 10.0)
         return synth.random_field(vg.n, seed=1), vg, cg
     raise ValueError(name)
 
